@@ -1,0 +1,174 @@
+// factor.cu -- FP64 tiled right-looking Cholesky (Section 3.1, Fig. 1) under
+// the two GPU schedules of Section 3.2:
+//
+//  * fork-join: for each block column J, one launch for POTRF(J), one grid
+//    with a CTA per TRSM(I, J), one grid with a CTA per trailing tile
+//    (collapsed: every (I, K) with J < K <= I, SYRK when I == K, else GEMM) or
+//    a CTA per block row I (naive: the CTA walks K = J+1 .. I).  Stream order
+//    is the barrier between the phases.
+//  * dataflow: one persistent kernel.  Every task (I, K, J) owns a counter of
+//    finished predecessors; a finished task increments the counters of its
+//    successors and pushes those that became ready onto a global ready queue
+//    that the CTAs pop.  No barrier ends a step.  Each tile receives its
+//    updates in ascending J (the chain dependency), exactly as under
+//    fork-join, so the two schedules produce identical bits.
+#include "common.cuh"
+#include "factor_impl.cuh"
+
+namespace chol {
+
+template struct TileStore<double>;
+
+// Allocation layout of one FP64 factorization.
+struct FactorWs {
+    void *base = nullptr;
+    double *store = nullptr;
+    Control *ctl = nullptr;
+    unsigned long long *queue = nullptr;
+    int32_t *deps = nullptr;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static int factor_fp64_device(int64_t n, double *A, int64_t lda, const chol_opts &o, int64_t *info,
+                              chol_stats *stats) {
+    const int64_t nb = o.nb > 0 ? o.nb : chol_default_nb(n, CHOL_FP64);
+    CHOL_CHECK_ARG(nb >= 1 && nb <= 2048, "nb must be in [1, 2048]");
+    const int64_t M = (n + nb - 1) / nb;
+    CHOL_CHECK_ARG(M < 65536, "too many tiles per dimension (n / nb must be < 65536)");
+    int sched = o.schedule == CHOL_SCHED_AUTO ? CHOL_SCHED_DATAFLOW : o.schedule;
+    CHOL_CHECK_ARG(sched >= CHOL_SCHED_FORK_JOIN && sched <= CHOL_SCHED_DATAFLOW, "unknown schedule");
+    cudaStream_t st = (cudaStream_t)o.stream;
+    prepare_pool();
+
+    const int64_t ntasks = num_tasks(M);
+    const size_t store_bytes = align256((size_t)num_tiles(M) * nb * nb * sizeof(double));
+    const size_t ctl_bytes = align256(sizeof(Control));
+    const size_t q_bytes = sched == CHOL_SCHED_DATAFLOW ? align256((size_t)2 * ntasks * 8) : 0;
+    const size_t d_bytes = sched == CHOL_SCHED_DATAFLOW ? align256((size_t)ntasks * 4) : 0;
+    FactorWs ws;
+    CHOL_CUDA(cudaMallocAsync(&ws.base, store_bytes + ctl_bytes + q_bytes + d_bytes, st));
+    char *p = (char *)ws.base;
+    ws.store = (double *)p;
+    ws.ctl = (Control *)(p + store_bytes);
+    ws.queue = (unsigned long long *)(p + store_bytes + ctl_bytes);
+    ws.deps = (int32_t *)(p + store_bytes + ctl_bytes + q_bytes);
+
+    int rc = CHOL_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    Control h{};
+    int launches = 0;
+    do {
+        if ((rc = launch_repack<double, double>(A, lda, n, ws.store, (int)nb, M, st)) != CHOL_OK) break;
+        if (cudaMemsetAsync(ws.ctl, 0, sizeof(Control), st) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__); break; }
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "event", __FILE__, __LINE__); break; }
+        TileStore<double> S{ws.store, (int32_t)nb, (int32_t)M};
+        SchedArgs a{ws.ctl, o.trace, o.trace_capacity, o.flags, 0};
+        if (sched == CHOL_SCHED_DATAFLOW) {
+            rc = run_dataflow<double>(S, a, ws.queue, ws.deps, o, st, &launches, e0);
+        } else {
+            cudaEventRecord(e0, st);
+            rc = run_fork_join<double>(S, a, sched == CHOL_SCHED_FORK_JOIN_NAIVE, st, &launches);
+        }
+        if (rc != CHOL_OK) break;
+        cudaEventRecord(e1, st);
+        if ((rc = launch_unpack<double, double>(ws.store, (int)nb, M, A, lda, n, st)) != CHOL_OK) break;
+        if (cudaMemcpyAsync(&h, ws.ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "readback", __FILE__, __LINE__); break; }
+        if (cudaStreamSynchronize(st) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "sync", __FILE__, __LINE__); break; }
+    } while (0);
+    cudaFreeAsync(ws.base, st);
+    if (rc == CHOL_OK) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *info = h.info;
+        if (stats) {
+            for (int i = 0; i < 4; ++i) stats->tasks[i] = (int64_t)h.tasks[i];
+            stats->nb = nb;
+            stats->schedule = sched;
+            stats->launches = launches;
+            stats->trace_records = (int64_t)h.trace_count;
+            stats->device_ms = ms;
+        }
+        if (h.status != 0) {
+            set_error("device-side wait expired after %.3f s (site %d)", o.timeout_s, h.timeout_where);
+            rc = h.status;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
+}
+
+}  // namespace chol
+
+using namespace chol;
+
+static thread_local int64_t g_last_info = 0;
+
+extern "C" {
+
+int chol_factor_ex(int64_t n, double *A, int64_t lda, const chol_opts *opts, int64_t *info,
+                   chol_stats *stats) {
+    CHOL_CHECK_ARG(info != nullptr, "info is NULL");
+    *info = 0;
+    CHOL_CHECK_ARG(n >= 0, "n < 0");
+    CHOL_CHECK_ARG(lda >= (n > 1 ? n : 1), "lda < max(1, n)");
+    chol_opts o = resolve_opts(opts);
+    CHOL_CHECK_ARG(o.precision == CHOL_FP64, "chol_factor_ex computes in FP64; use chol_mixed_factor");
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (n == 0) return CHOL_OK;
+    CHOL_CHECK_ARG(A != nullptr, "A is NULL");
+    return factor_fp64_device(n, A, lda, o, info, stats);
+}
+
+int chol_factor(int64_t n, int64_t nb, double *A, int64_t lda) {
+    chol_opts o;
+    chol_opts_init(&o);
+    o.nb = nb;
+    o.schedule = CHOL_SCHED_DATAFLOW;
+    CHOL_CHECK_ARG(nb >= 1, "nb < 1");
+    int64_t info = 0;
+    const int rc = chol_factor_ex(n, A, lda, &o, &info, nullptr);
+    g_last_info = info;
+    if (rc == CHOL_OK && info > 0) {
+        set_error("matrix is not positive definite: leading minor %lld", (long long)info);
+        return CHOL_ERR_NOT_SPD;
+    }
+    return rc;
+}
+
+int64_t chol_last_info(void) { return g_last_info; }
+
+int chol_factor_host(int64_t n, double *A_host, int64_t lda, const chol_opts *opts, int64_t *info,
+                     chol_stats *stats) {
+    CHOL_CHECK_ARG(info != nullptr, "info is NULL");
+    *info = 0;
+    CHOL_CHECK_ARG(n >= 0, "n < 0");
+    CHOL_CHECK_ARG(lda >= (n > 1 ? n : 1), "lda < max(1, n)");
+    if (n == 0) return CHOL_OK;
+    CHOL_CHECK_ARG(A_host != nullptr, "A is NULL");
+    chol_opts o = resolve_opts(opts);
+    cudaStream_t st = (cudaStream_t)o.stream;
+    prepare_pool();
+    double *dA = nullptr;
+    CHOL_CUDA(cudaMallocAsync(&dA, (size_t)n * n * sizeof(double), st));
+    int rc = CHOL_OK;
+    do {
+        if (cudaMemcpy2DAsync(dA, n * sizeof(double), A_host, lda * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "H2D", __FILE__, __LINE__);
+            break;
+        }
+        if ((rc = chol_factor_ex(n, dA, n, &o, info, stats)) != CHOL_OK) break;
+        if (cudaMemcpy2DAsync(A_host, lda * sizeof(double), dA, n * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "D2H", __FILE__, __LINE__);
+            break;
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "sync", __FILE__, __LINE__);
+    } while (0);
+    cudaFreeAsync(dA, st);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,426 @@
+// factor_impl.cuh -- the schedule machinery shared by the FP64, FP32-batched
+// and mixed-precision factorizations: tile-store repack/unpack, fork-join
+// kernels, and the persistent dataflow kernel with its ready queues.
+//
+// A "Body" policy supplies the task bodies (which engine runs POTRF, TRSM,
+// SYRK and GEMM) and the geometry of the matrices it factors:
+//   using Args; using Smem;
+//   static __device__ int  tiles(const Args &, int m);          // M of matrix m
+//   static __device__ int64_t task_base(const Args &, int m);   // offset of m's task ids
+//   static __device__ void run(const Args &, const SchedArgs &, int m, int I, int K, int J, Smem &);
+//   static constexpr bool kSolveTask;  // a SOLVE task follows POTRF(M-1) of every matrix
+//   static __device__ void solve(const Args &, const SchedArgs &, int m, Smem &);
+#pragma once
+
+#include "common.cuh"
+#include "simt_tiles.cuh"
+
+namespace chol {
+
+template <typename T>
+struct TileStore {
+    T *base;
+    int32_t nb;
+    int32_t M;
+    __device__ __forceinline__ T *tile(int I, int K) const {
+        return base + (size_t)tile_index(I, K) * (size_t)nb * (size_t)nb;
+    }
+};
+
+struct SchedArgs {
+    Control *ctl;
+    chol_trace_rec *trace;
+    int64_t trace_cap;
+    int32_t flags;
+    int32_t pad;
+};
+
+struct DFArgs {
+    unsigned long long *queue;   // 2 * capacity slots: [0, cap) priority, [cap, 2 cap) normal
+    int32_t *deps;               // one counter per task
+    int64_t capacity;            // slots per queue (>= total tasks)
+    int64_t total;               // tasks to run before the kernel ends
+    uint64_t timeout_ns;
+    int32_t num_matrices;
+    int32_t pad;
+};
+
+constexpr int kSolveJ = 0xFFFF;  // J marker of the fused SOLVE task (batched)
+
+// ----------------------------------------------------------------- repack / unpack
+// (I, K) of lower tile index t = I (I + 1) / 2 + K
+__device__ __forceinline__ void tile_of(int64_t t, int &I, int &K) {
+    int64_t i = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((i + 1) * (i + 2) / 2 <= t) ++i;
+    while (i * (i + 1) / 2 > t) --i;
+    I = (int)i;
+    K = (int)(t - i * (i + 1) / 2);
+}
+
+// Column-major lower(A) -> row-major tiles; entries outside the n x n matrix
+// are the identity; the strict upper triangle of diagonal tiles is set to 0
+// (A's upper triangle is never read).  grid.x = tile, grid.y = 32 x 32 sub-block.
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) repack_kernel(const Tin *A, int64_t lda, int64_t n, Tout *store,
+                                                     int nb, int64_t tile0) {
+    __shared__ Tout buf[32][33];
+    int I, K;
+    const int64_t t = tile0 + blockIdx.x;
+    tile_of(t, I, K);
+    const int nsb = (nb + 31) / 32;
+    const int sr = blockIdx.y / nsb, sc = blockIdx.y % nsb;
+    Tout *tile = store + (size_t)t * nb * nb;
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
+        const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
+        Tout v = Tout(0);
+        if (r < nb && c < nb) {
+            if (i < n && j < n) v = j <= i ? (Tout)A[j * lda + i] : Tout(0);
+            else v = i == j ? Tout(1) : Tout(0);
+        }
+        buf[yy][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
+        if (r < nb && c < nb) tile[(size_t)r * nb + c] = buf[threadIdx.x][yy];
+    }
+}
+
+// Row-major tiles -> lower triangle of column-major A (i >= j, i, j < n).
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(256) unpack_kernel(const Tin *store, int nb, Tout *A, int64_t lda, int64_t n,
+                                                     int64_t tile0) {
+    __shared__ Tin buf[32][33];
+    int I, K;
+    const int64_t t = tile0 + blockIdx.x;
+    tile_of(t, I, K);
+    const int nsb = (nb + 31) / 32;
+    const int sr = blockIdx.y / nsb, sc = blockIdx.y % nsb;
+    const Tin *tile = store + (size_t)t * nb * nb;
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
+        buf[yy][threadIdx.x] = (r < nb && c < nb) ? tile[(size_t)r * nb + c] : Tin(0);
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += 8) {
+        const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
+        const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
+        if (r < nb && c < nb && i < n && j < n && j <= i) A[j * lda + i] = (Tout)buf[threadIdx.x][yy];
+    }
+}
+
+template <typename Tin, typename Tout>
+int launch_repack(const Tin *A, int64_t lda, int64_t n, Tout *store, int nb, int64_t M, cudaStream_t st) {
+    const int nsb = (nb + 31) / 32;
+    const int64_t tiles = num_tiles(M);
+    for (int64_t t0 = 0; t0 < tiles; t0 += 1ll << 30) {
+        const int64_t cnt = tiles - t0 < (1ll << 30) ? tiles - t0 : (1ll << 30);
+        repack_kernel<Tin, Tout><<<dim3((unsigned)cnt, nsb * nsb), dim3(32, 8), 0, st>>>(A, lda, n, store, nb, t0);
+    }
+    CHOL_CUDA(cudaGetLastError());
+    return CHOL_OK;
+}
+
+template <typename Tin, typename Tout>
+int launch_unpack(const Tin *store, int nb, int64_t M, Tout *A, int64_t lda, int64_t n, cudaStream_t st) {
+    const int nsb = (nb + 31) / 32;
+    const int64_t tiles = num_tiles(M);
+    for (int64_t t0 = 0; t0 < tiles; t0 += 1ll << 30) {
+        const int64_t cnt = tiles - t0 < (1ll << 30) ? tiles - t0 : (1ll << 30);
+        unpack_kernel<Tin, Tout><<<dim3((unsigned)cnt, nsb * nsb), dim3(32, 8), 0, st>>>(store, nb, A, lda, n, t0);
+    }
+    CHOL_CUDA(cudaGetLastError());
+    return CHOL_OK;
+}
+
+// ----------------------------------------------------------------- task bookkeeping
+__device__ __forceinline__ void task_done_bookkeeping(const SchedArgs &a, int type, int m, int I, int K, int J,
+                                                      uint64_t t0) {
+    // thread 0 only
+    atomicAdd(&a.ctl->tasks[type & 3], 1ull);
+    if (a.trace) {
+        const unsigned long long slot = atomicAdd(&a.ctl->trace_count, 1ull);
+        if ((int64_t)slot < a.trace_cap) {
+            chol_trace_rec r;
+            r.type = type;
+            r.I = I;
+            r.K = K;
+            r.J = J;
+            r.sm = (int32_t)smid();
+            r.matrix = m;
+            r.t_start = t0;
+            r.t_end = global_ns();
+            a.trace[slot] = r;
+        }
+    }
+}
+
+// ----------------------------------------------------------------- SIMT body (FP64 / FP32)
+template <typename T>
+struct SimtBody {
+    struct Args {
+        TileStore<T> S;
+    };
+    using Smem = SimtSmem<T>;
+    static constexpr bool kSolveTask = false;
+    static __device__ __forceinline__ int tiles(const Args &a, int) { return a.S.M; }
+    static __device__ __forceinline__ int64_t task_base(const Args &, int) { return 0; }
+    static __device__ void run(const Args &g, const SchedArgs &a, int m, int I, int K, int J, Smem &sm) {
+        const int type = task_type(I, K, J);
+        uint64_t t0 = 0;
+        if (a.trace && threadIdx.x == 0) t0 = global_ns();
+        const TileStore<T> &S = g.S;
+        if (!(a.flags & CHOL_FLAG_NOOP)) {
+            switch (type) {
+            case T_POTRF: {
+                const int li = tile_potrf(S.tile(J, J), S.nb, sm);
+                if (li && threadIdx.x == 0) {
+                    report_info(a.ctl, (int64_t)J * S.nb + li);
+                    st_release_s32(&a.ctl->abort, 1);
+                }
+            } break;
+            case T_TRSM: tile_trsm(S.tile(I, J), S.tile(J, J), S.nb, sm); break;
+            case T_SYRK: tile_syrk(S.tile(I, I), S.tile(I, J), S.nb, sm); break;
+            default: tile_gemm(S.tile(I, K), S.tile(I, J), S.tile(K, J), S.nb, sm); break;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) task_done_bookkeeping(a, type, m, I, K, J, t0);
+    }
+    static __device__ void solve(const Args &, const SchedArgs &, int, Smem &) {}
+};
+
+// ----------------------------------------------------------------- fork-join kernels
+template <class Body>
+__global__ void __launch_bounds__(256) fj_potrf_kernel(typename Body::Args g, SchedArgs a, int J) {
+    __shared__ typename Body::Smem sm;
+    if (ld_acquire_s32(&a.ctl->abort)) return;
+    Body::run(g, a, 0, J, J, J, sm);
+}
+
+template <class Body>
+__global__ void __launch_bounds__(256) fj_trsm_kernel(typename Body::Args g, SchedArgs a, int J) {
+    __shared__ typename Body::Smem sm;
+    if (ld_acquire_s32(&a.ctl->abort)) return;
+    Body::run(g, a, 0, J + 1 + (int)blockIdx.x, J, J, sm);
+}
+
+// collapsed: one CTA per trailing lower tile (I, K), J < K <= I
+template <class Body>
+__global__ void __launch_bounds__(256) fj_update_kernel(typename Body::Args g, SchedArgs a, int J) {
+    __shared__ typename Body::Smem sm;
+    if (ld_acquire_s32(&a.ctl->abort)) return;
+    int i, k;
+    tile_of(blockIdx.x, i, k);
+    Body::run(g, a, 0, J + 1 + i, J + 1 + k, J, sm);
+}
+
+// naive: one CTA per block row I walks K = J+1 .. I (SYRK last)
+template <class Body>
+__global__ void __launch_bounds__(256) fj_update_naive_kernel(typename Body::Args g, SchedArgs a, int J) {
+    __shared__ typename Body::Smem sm;
+    if (ld_acquire_s32(&a.ctl->abort)) return;
+    const int I = J + 1 + (int)blockIdx.x;
+    for (int K = J + 1; K <= I; ++K) Body::run(g, a, 0, I, K, J, sm);
+}
+
+template <class Body>
+int run_fork_join(const typename Body::Args &g, const SchedArgs &a, int M, bool naive, cudaStream_t st,
+                  int *launches) {
+    int L = 0;
+    for (int J = 0; J < M; ++J) {
+        fj_potrf_kernel<Body><<<1, kThreads, 0, st>>>(g, a, J);
+        ++L;
+        const int rest = M - J - 1;
+        if (rest > 0) {
+            fj_trsm_kernel<Body><<<rest, kThreads, 0, st>>>(g, a, J);
+            if (naive)
+                fj_update_naive_kernel<Body><<<rest, kThreads, 0, st>>>(g, a, J);
+            else
+                fj_update_kernel<Body><<<(unsigned)((int64_t)rest * (rest + 1) / 2), kThreads, 0, st>>>(g, a, J);
+            L += 2;
+        }
+    }
+    *launches = L;
+    CHOL_CUDA(cudaGetLastError());
+    return CHOL_OK;
+}
+
+// ----------------------------------------------------------------- dataflow scheduler
+__device__ __forceinline__ void df_timeout(Control *ctl, int where) {
+    if (atomicCAS(&ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) ctl->timeout_where = where;
+    st_release_s32(&ctl->abort, 1);
+}
+
+__device__ __forceinline__ void df_push(Control *ctl, const DFArgs &d, int q, uint64_t v) {
+    const unsigned long long slot = atomicAdd(&ctl->tail[q], 1ull);
+    st_release_u64(&d.queue[(size_t)q * d.capacity + slot], v);
+}
+
+// Pop one task (thread 0).  Returns 1 (task in *out), 0 (all tasks done) or
+// -1 (abort, failure elsewhere, or a wait longer than the timeout).
+__device__ int df_pop(Control *ctl, const DFArgs &d, uint64_t *out) {
+    const uint64_t t0 = global_ns();
+    uint32_t backoff = 64;
+    for (;;) {
+        if (ld_acquire_s32(&ctl->abort)) return -1;
+        if (ld_relaxed_u64(&ctl->completed) >= (uint64_t)d.total) return 0;
+        bool retry = false;
+        for (int q = 0; q < 2 && !retry; ++q) {
+            const unsigned long long h = ld_relaxed_u64(&ctl->head[q]);
+            const unsigned long long t = ld_acquire_u64(&ctl->tail[q]);
+            if (h < t) {
+                if (atomicCAS(&ctl->head[q], h, h + 1) == h) {
+                    const unsigned long long *slot = &d.queue[(size_t)q * d.capacity + h];
+                    uint64_t v;
+                    // the pusher reserved this slot before we saw it: it is written shortly
+                    while ((v = ld_acquire_u64(slot)) == kEmptySlot) {
+                        if (global_ns() - t0 > d.timeout_ns) {
+                            df_timeout(ctl, 2);
+                            return -1;
+                        }
+                    }
+                    *out = v;
+                    return 1;
+                }
+                retry = true;  // lost the race for this slot: look again at once
+            }
+        }
+        if (retry) continue;
+        if (global_ns() - t0 > d.timeout_ns) {
+            df_timeout(ctl, 1);
+            return -1;
+        }
+        nanosleep_ns(backoff);
+        backoff = backoff < 2048 ? backoff * 2 : 2048;
+    }
+}
+
+template <class Body>
+__device__ __forceinline__ void df_notify_one(const typename Body::Args &g, const SchedArgs &a, const DFArgs &d,
+                                              int m, int M, int I, int K, int J) {
+    if ((a.flags & CHOL_FLAG_TEST_WITHHOLD) && I == M - 1 && K == M - 1 && J == M - 1) return;
+    const int32_t need = task_needs(I, K, J);
+    const int64_t id = Body::task_base(g, m) + task_id(I, K, J);
+    const int32_t old = atom_add_acqrel_s32(&d.deps[id], 1);
+    if (old + 1 == need) {
+        const int type = task_type(I, K, J);
+        const int q = ((a.flags & CHOL_FLAG_PRIORITY) && type != T_GEMM) ? 0 : 1;
+        df_push(a.ctl, d, q, pack_task(m, I, K, J));
+    }
+}
+
+// Successors of task (I, K, J) of matrix m, released by the 32 lanes of warp 0.
+template <class Body>
+__device__ void df_notify(const typename Body::Args &g, const SchedArgs &a, const DFArgs &d, int m, int I, int K,
+                          int J, int lane) {
+    const int M = Body::tiles(g, m);
+    if (J < K) {                       // an update: the next task of the tile's chain
+        if (lane == 0) df_notify_one<Body>(g, a, d, m, M, I, K, J + 1);
+    } else if (I == K) {               // POTRF(K): every TRSM(I2, K)
+        for (int I2 = K + 1 + lane; I2 < M; I2 += 32) df_notify_one<Body>(g, a, d, m, M, I2, K, K);
+        if (Body::kSolveTask && K == M - 1 && lane == 0) df_push(a.ctl, d, 0, pack_task(m, M, M, kSolveJ));
+    } else {                           // TRSM(I, K): SYRK(I,I,K), GEMM(I,K2,K) for K<K2<I, GEMM(I2,I,K) for I2>I
+        const int cnt = 1 + (I - K - 1) + (M - I - 1);
+        for (int idx = lane; idx < cnt; idx += 32) {
+            if (idx == 0) df_notify_one<Body>(g, a, d, m, M, I, I, K);
+            else if (idx < I - K) df_notify_one<Body>(g, a, d, m, M, I, K + idx, K);
+            else df_notify_one<Body>(g, a, d, m, M, I + 1 + (idx - (I - K)), I, K);
+        }
+    }
+}
+
+template <class Body>
+__global__ void __launch_bounds__(256) df_kernel(typename Body::Args g, SchedArgs a, DFArgs d) {
+    __shared__ typename Body::Smem sm;
+    __shared__ unsigned long long s_task;
+    __shared__ int s_cmd;
+    Control *ctl = a.ctl;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            uint64_t v = 0;
+            const int cmd = df_pop(ctl, d, &v);
+            if (cmd == 1) fence_acq_rel();
+            s_task = v;
+            s_cmd = cmd;
+        }
+        __syncthreads();
+        const int cmd = s_cmd;
+        const uint64_t v = s_task;
+        __syncthreads();
+        if (cmd != 1) break;
+        const int J = (int)(v & 0xffff), K = (int)((v >> 16) & 0xffff), I = (int)((v >> 32) & 0xffff);
+        const int m = (int)(v >> 48);
+        if (J == kSolveJ) {
+            Body::solve(g, a, m, sm);
+        } else {
+            Body::run(g, a, m, I, K, J, sm);   // ends with __syncthreads()
+        }
+        if (threadIdx.x < 32) {
+            fence_acq_rel();                   // publish this CTA's tile writes (cumulative after the barrier)
+            __syncwarp();
+            if (J != kSolveJ && !ld_relaxed_s32(&ctl->abort)) df_notify<Body>(g, a, d, m, I, K, J, threadIdx.x);
+            __syncwarp();
+            if (threadIdx.x == 0) atomicAdd(&ctl->completed, 1ull);
+        }
+    }
+}
+
+// Seed the queues with POTRF(0) of every matrix.
+__global__ void df_seed_kernel(Control *ctl, DFArgs d, int flags) {
+    const int q = (flags & CHOL_FLAG_PRIORITY) ? 0 : 1;
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < d.num_matrices; m += gridDim.x * blockDim.x)
+        d.queue[(size_t)q * d.capacity + m] = pack_task(m, 0, 0, 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->tail[q] = (unsigned long long)d.num_matrices;
+}
+
+template <class Body>
+int df_grid(int num_ctas) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, df_kernel<Body>, kThreads, 0) != cudaSuccess || occ < 1)
+        occ = 1;
+    const int sms = num_sms();
+    const int maxg = sms * occ;
+    if (num_ctas <= 0) return sms;
+    return num_ctas < maxg ? num_ctas : maxg;
+}
+
+// Prepare counters and queues (stream-ordered), then launch the persistent
+// kernel; `e0` (if not null) is recorded between the two, so events around
+// the launch time the schedule alone.
+template <class Body>
+int launch_dataflow(const typename Body::Args &g, const SchedArgs &a, DFArgs d, const chol_opts &o,
+                    cudaStream_t st, int *launches, cudaEvent_t e0 = nullptr) {
+    CHOL_CUDA(cudaMemsetAsync(d.queue, 0xFF, (size_t)2 * d.capacity * sizeof(unsigned long long), st));
+    CHOL_CUDA(cudaMemsetAsync(d.deps, 0, (size_t)d.total * sizeof(int32_t), st));
+    d.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
+    df_seed_kernel<<<(d.num_matrices + 255) / 256, 256, 0, st>>>(a.ctl, d, a.flags);
+    if (e0) CHOL_CUDA(cudaEventRecord(e0, st));
+    df_kernel<Body><<<df_grid<Body>(o.num_ctas), kThreads, 0, st>>>(g, a, d);
+    *launches = 2;
+    CHOL_CUDA(cudaGetLastError());
+    return CHOL_OK;
+}
+
+// single-matrix FP64 / FP32 helpers used by factor.cu
+template <typename T>
+int run_fork_join(const TileStore<T> &S, const SchedArgs &a, bool naive, cudaStream_t st, int *launches) {
+    typename SimtBody<T>::Args g{S};
+    return run_fork_join<SimtBody<T>>(g, a, S.M, naive, st, launches);
+}
+
+template <typename T>
+int run_dataflow(const TileStore<T> &S, const SchedArgs &a, unsigned long long *queue, int32_t *deps,
+                 const chol_opts &o, cudaStream_t st, int *launches, cudaEvent_t e0) {
+    typename SimtBody<T>::Args g{S};
+    DFArgs d{};
+    d.queue = queue;
+    d.deps = deps;
+    d.capacity = num_tasks(S.M);
+    d.total = num_tasks(S.M);
+    d.num_matrices = 1;
+    return launch_dataflow<SimtBody<T>>(g, a, d, o, st, launches, e0);
+}
+
+}  // namespace chol
