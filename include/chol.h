@@ -196,6 +196,10 @@ int chol_mixed_get_factor(chol_factor_h h, double *L, int64_t ldl);
 
 void chol_factor_free(chol_factor_h h);
 
+/* Statistics (tasks executed, tile order, schedule, device time of the
+ * schedule kernels) of the last chol_mixed_factor call on this thread. */
+int chol_mixed_last_stats(chol_stats *stats);
+
 /* ----------------------------------------------------------------- batched */
 
 typedef struct chol_batch_s *chol_batch_h;

@@ -1,0 +1,34 @@
+/*
+ * chol_testing.h -- test hooks of libchol.so.  Not part of the factorization
+ * API; they expose single kernels so tests can check them in isolation.
+ */
+#ifndef CHOL_TESTING_H
+#define CHOL_TESTING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One tcgen05 SYRK/GEMM tile update, the tensor-core kernel of the
+ * mixed-precision trailing update (Section 3.1 SYRK and GEMM formulas,
+ * A_IK <- A_IK - A_IJ A_KJ^T), run twice by one CTA:
+ *     C[r] <- C[r] - 2^-eA 2^-eB sum_p A_p B_p^T,   r = 0, 1
+ * precision: CHOL_BF16 / CHOL_FP16 (one product of 16-bit operands),
+ * CHOL_TF32 (one product of tf32-valued binary32 operands) or CHOL_FP32
+ * (three products hi*hi + hi*lo + lo*hi).  nb in {128, 256, 512, 1024}.
+ * ops (device): the hi operand array of 2*nb rows x nb columns, row-major
+ * (rows [0, nb) = A, rows [nb, 2 nb) = B), 2-byte elements for BF16/FP16 and
+ * 4-byte for TF32/FP32; for CHOL_FP32 the lo array of the same shape follows.
+ * C (device): two row-major nb x nb binary32 tiles, contiguous.  lower != 0:
+ * only the sub-tiles on or below the diagonal are updated (SYRK).
+ * Returns CHOL_OK, CHOL_ERR_ARG, CHOL_ERR_CUDA or CHOL_ERR_TIMEOUT (a bounded
+ * wait expired). */
+int chol_test_tc_update(int32_t precision, int64_t nb, const void *ops, int32_t eA, int32_t eB, float *C,
+                        int32_t lower);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -82,6 +82,8 @@ SIGNATURES = {
     "chol_mixed_solve": (ctypes.c_int, [_vp, _i64, _vp, _i64, _vp, _i64, _P(_i32), _P(_dbl)]),
     "chol_mixed_get_factor": (ctypes.c_int, [_vp, _vp, _i64]),
     "chol_factor_free": (None, [_vp]),
+    "chol_mixed_last_stats": (ctypes.c_int, [_P(chol_stats)]),
+    "chol_test_tc_update": (ctypes.c_int, [_i32, _i64, _vp, _i32, _i32, _vp, _i32]),
     "chol_batch_plan": (ctypes.c_int, [_i32, _P(_i64), _P(chol_opts), _P(_vp)]),
     "chol_batch_run": (ctypes.c_int, [_vp, _P(_vp), _P(_i64), _P(_vp), _P(_i64)]),
     "chol_batch_stats": (ctypes.c_int, [_vp, _P(chol_stats)]),
@@ -290,6 +292,17 @@ class MixedFactor:
             self.close()
         except Exception:
             pass
+
+
+def chol_mixed_last_stats() -> chol_stats:
+    st = chol_stats()
+    _check(lib().chol_mixed_last_stats(ctypes.byref(st)), "chol_mixed_last_stats")
+    return st
+
+
+def chol_test_tc_update(precision, nb: int, ops, eA: int, eB: int, C, lower: bool = False) -> int:
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return lib().chol_test_tc_update(p, int(nb), _ptr(ops), int(eA), int(eB), _ptr(C), int(bool(lower)))
 
 
 def chol_mixed_factor(A, o: chol_opts | None = None, raise_on_error: bool = True):

@@ -164,6 +164,9 @@ struct SimtBody {
     };
     using Smem = SimtSmem<T>;
     static constexpr bool kSolveTask = false;
+    static constexpr size_t kSmemBytes = sizeof(SimtSmem<T>);
+    static __device__ __forceinline__ void cta_init(const Args &, Smem &) {}
+    static __device__ __forceinline__ void cta_fini(const Args &, Smem &) {}
     static __device__ __forceinline__ int tiles(const Args &a, int) { return a.S.M; }
     static __device__ __forceinline__ int64_t task_base(const Args &, int) { return 0; }
     static __device__ void run(const Args &g, const SchedArgs &a, int m, int I, int K, int J, Smem &sm) {
@@ -192,53 +195,87 @@ struct SimtBody {
 };
 
 // ----------------------------------------------------------------- fork-join kernels
+// Dynamic shared memory, aligned to 1024 bytes (the tcgen05 bodies stage
+// swizzled operand tiles in it); launched with Body::kSmemBytes + 1024.
 template <class Body>
-__global__ void __launch_bounds__(256) fj_potrf_kernel(typename Body::Args g, SchedArgs a, int J) {
-    __shared__ typename Body::Smem sm;
+__device__ __forceinline__ typename Body::Smem &body_smem() {
+    extern __shared__ uint8_t dyn_smem[];
+    const uintptr_t p = (reinterpret_cast<uintptr_t>(dyn_smem) + 1023) & ~uintptr_t(1023);
+    return *reinterpret_cast<typename Body::Smem *>(p);
+}
+template <class Body>
+constexpr size_t body_smem_bytes() { return Body::kSmemBytes + 1024; }
+
+template <class Body>
+__global__ void __launch_bounds__(256) fj_potrf_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
+                                                       int J) {
+    typename Body::Smem &sm = body_smem<Body>();
     if (ld_acquire_s32(&a.ctl->abort)) return;
+    Body::cta_init(g, sm);
     Body::run(g, a, 0, J, J, J, sm);
+    Body::cta_fini(g, sm);
 }
 
 template <class Body>
-__global__ void __launch_bounds__(256) fj_trsm_kernel(typename Body::Args g, SchedArgs a, int J) {
-    __shared__ typename Body::Smem sm;
+__global__ void __launch_bounds__(256) fj_trsm_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
+                                                      int J) {
+    typename Body::Smem &sm = body_smem<Body>();
     if (ld_acquire_s32(&a.ctl->abort)) return;
+    Body::cta_init(g, sm);
     Body::run(g, a, 0, J + 1 + (int)blockIdx.x, J, J, sm);
+    Body::cta_fini(g, sm);
 }
 
 // collapsed: one CTA per trailing lower tile (I, K), J < K <= I
 template <class Body>
-__global__ void __launch_bounds__(256) fj_update_kernel(typename Body::Args g, SchedArgs a, int J) {
-    __shared__ typename Body::Smem sm;
+__global__ void __launch_bounds__(256) fj_update_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
+                                                        int J) {
+    typename Body::Smem &sm = body_smem<Body>();
     if (ld_acquire_s32(&a.ctl->abort)) return;
     int i, k;
     tile_of(blockIdx.x, i, k);
+    Body::cta_init(g, sm);
     Body::run(g, a, 0, J + 1 + i, J + 1 + k, J, sm);
+    Body::cta_fini(g, sm);
 }
 
 // naive: one CTA per block row I walks K = J+1 .. I (SYRK last)
 template <class Body>
-__global__ void __launch_bounds__(256) fj_update_naive_kernel(typename Body::Args g, SchedArgs a, int J) {
-    __shared__ typename Body::Smem sm;
+__global__ void __launch_bounds__(256) fj_update_naive_kernel(const __grid_constant__ typename Body::Args g,
+                                                              SchedArgs a, int J) {
+    typename Body::Smem &sm = body_smem<Body>();
     if (ld_acquire_s32(&a.ctl->abort)) return;
     const int I = J + 1 + (int)blockIdx.x;
+    Body::cta_init(g, sm);
     for (int K = J + 1; K <= I; ++K) Body::run(g, a, 0, I, K, J, sm);
+    Body::cta_fini(g, sm);
+}
+
+template <class Body, typename KernelT>
+int set_smem_attr(KernelT kernel) {
+    CHOL_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)body_smem_bytes<Body>()));
+    return CHOL_OK;
 }
 
 template <class Body>
 int run_fork_join(const typename Body::Args &g, const SchedArgs &a, int M, bool naive, cudaStream_t st,
                   int *launches) {
+    int rc;
+    if ((rc = set_smem_attr<Body>(fj_potrf_kernel<Body>)) || (rc = set_smem_attr<Body>(fj_trsm_kernel<Body>)) ||
+        (rc = set_smem_attr<Body>(fj_update_kernel<Body>)) || (rc = set_smem_attr<Body>(fj_update_naive_kernel<Body>)))
+        return rc;
+    const size_t smem = body_smem_bytes<Body>();
     int L = 0;
     for (int J = 0; J < M; ++J) {
-        fj_potrf_kernel<Body><<<1, kThreads, 0, st>>>(g, a, J);
+        fj_potrf_kernel<Body><<<1, kThreads, smem, st>>>(g, a, J);
         ++L;
         const int rest = M - J - 1;
         if (rest > 0) {
-            fj_trsm_kernel<Body><<<rest, kThreads, 0, st>>>(g, a, J);
+            fj_trsm_kernel<Body><<<rest, kThreads, smem, st>>>(g, a, J);
             if (naive)
-                fj_update_naive_kernel<Body><<<rest, kThreads, 0, st>>>(g, a, J);
+                fj_update_naive_kernel<Body><<<rest, kThreads, smem, st>>>(g, a, J);
             else
-                fj_update_kernel<Body><<<(unsigned)((int64_t)rest * (rest + 1) / 2), kThreads, 0, st>>>(g, a, J);
+                fj_update_kernel<Body><<<(unsigned)((int64_t)rest * (rest + 1) / 2), kThreads, smem, st>>>(g, a, J);
             L += 2;
         }
     }
@@ -260,7 +297,7 @@ __device__ __forceinline__ void df_push(Control *ctl, const DFArgs &d, int q, ui
 
 // Pop one task (thread 0).  Returns 1 (task in *out), 0 (all tasks done) or
 // -1 (abort, failure elsewhere, or a wait longer than the timeout).
-__device__ int df_pop(Control *ctl, const DFArgs &d, uint64_t *out) {
+static __device__ int df_pop(Control *ctl, const DFArgs &d, uint64_t *out) {
     const uint64_t t0 = global_ns();
     uint32_t backoff = 64;
     for (;;) {
@@ -332,11 +369,12 @@ __device__ void df_notify(const typename Body::Args &g, const SchedArgs &a, cons
 }
 
 template <class Body>
-__global__ void __launch_bounds__(256) df_kernel(typename Body::Args g, SchedArgs a, DFArgs d) {
-    __shared__ typename Body::Smem sm;
+__global__ void __launch_bounds__(256) df_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a, DFArgs d) {
+    typename Body::Smem &sm = body_smem<Body>();
     __shared__ unsigned long long s_task;
     __shared__ int s_cmd;
     Control *ctl = a.ctl;
+    Body::cta_init(g, sm);
     for (;;) {
         if (threadIdx.x == 0) {
             uint64_t v = 0;
@@ -365,10 +403,11 @@ __global__ void __launch_bounds__(256) df_kernel(typename Body::Args g, SchedArg
             if (threadIdx.x == 0) atomicAdd(&ctl->completed, 1ull);
         }
     }
+    Body::cta_fini(g, sm);
 }
 
 // Seed the queues with POTRF(0) of every matrix.
-__global__ void df_seed_kernel(Control *ctl, DFArgs d, int flags) {
+static __global__ void df_seed_kernel(Control *ctl, DFArgs d, int flags) {
     const int q = (flags & CHOL_FLAG_PRIORITY) ? 0 : 1;
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < d.num_matrices; m += gridDim.x * blockDim.x)
         d.queue[(size_t)q * d.capacity + m] = pack_task(m, 0, 0, 0);
@@ -378,7 +417,9 @@ __global__ void df_seed_kernel(Control *ctl, DFArgs d, int flags) {
 template <class Body>
 int df_grid(int num_ctas) {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, df_kernel<Body>, kThreads, 0) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, df_kernel<Body>, kThreads, body_smem_bytes<Body>()) !=
+            cudaSuccess ||
+        occ < 1)
         occ = 1;
     const int sms = num_sms();
     const int maxg = sms * occ;
@@ -396,8 +437,10 @@ int launch_dataflow(const typename Body::Args &g, const SchedArgs &a, DFArgs d, 
     CHOL_CUDA(cudaMemsetAsync(d.deps, 0, (size_t)d.total * sizeof(int32_t), st));
     d.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
     df_seed_kernel<<<(d.num_matrices + 255) / 256, 256, 0, st>>>(a.ctl, d, a.flags);
+    int rc;
+    if ((rc = set_smem_attr<Body>(df_kernel<Body>))) return rc;
     if (e0) CHOL_CUDA(cudaEventRecord(e0, st));
-    df_kernel<Body><<<df_grid<Body>(o.num_ctas), kThreads, 0, st>>>(g, a, d);
+    df_kernel<Body><<<df_grid<Body>(o.num_ctas), kThreads, body_smem_bytes<Body>(), st>>>(g, a, d);
     *launches = 2;
     CHOL_CUDA(cudaGetLastError());
     return CHOL_OK;

@@ -1,0 +1,689 @@
+// mixed.cu -- mixed-precision tiled Cholesky with FP64 iterative refinement.
+//
+// The tiles are kept in binary32.  POTRF of each diagonal tile runs in
+// binary64 (the tile is widened, factored, rounded back), TRSM in binary32 on
+// the CUDA cores, and its epilogue writes the tensor-core operand copies of
+// the panel tile: bf16 / fp16 after an exact power-of-two scaling that puts
+// the tile's largest magnitude in [2^14, 2^15), or tf32-rounded values (hi,
+// and lo = tf32(x - hi) for the 3-product FP32 mode).  SYRK and GEMM run on
+// tcgen05 with binary32 accumulation in tensor memory (tc_gemm.cuh).  Both
+// schedules of Section 3.2 run these bodies unchanged.
+//
+// Solves refine in FP64: r = b - A x with the caller's FP64 A, stop when the
+// normwise backward error reaches the tolerance, else correct x += d with
+// L^ L^T d = r solved in binary32 on the tile store.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "factor_impl.cuh"
+#include "solve_impl.cuh"
+#include "tc_gemm.cuh"
+
+namespace chol {
+
+// ------------------------------------------------------------------ tensor maps
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// 2-D map over `rows` rows of nb elements (row pitch nb * elem bytes), boxes of
+// 128 bytes of K x 128 rows, 128-byte swizzle.
+int make_operand_map(CUtensorMap *map, void *base, int fmt, int64_t rows, int64_t nb) {
+    auto enc = tensor_map_encoder();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return CHOL_ERR_CUDA;
+    }
+    const int eb = fmt == OP_TF32 ? 4 : 2;
+    const CUtensorMapDataType dt = fmt == OP_TF32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : fmt == OP_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    cuuint64_t dims[2] = {(cuuint64_t)nb, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(nb * eb)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)kBoxRows};
+    cuuint32_t estr[2] = {1, 1};
+    memset(map, 0, sizeof(*map));
+    CUresult r = enc(map, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return CHOL_ERR_CUDA;
+    }
+    return CHOL_OK;
+}
+
+static int op_fmt(int precision) {
+    return precision == CHOL_BF16 ? OP_BF16 : precision == CHOL_FP16 ? OP_F16 : OP_TF32;
+}
+
+// ------------------------------------------------------------------ task bodies
+struct MixedArgs {
+    CUtensorMap map_hi;        // operand copies (bf16 / fp16 / tf32-hi)
+    CUtensorMap map_lo;        // tf32-lo (FP32 mode)
+    TileStore<float> S;        // binary32 tiles
+    void *op_hi;               // operand stores, same tile indexing as S
+    float *op_lo;
+    int32_t *exps;             // per-tile scaling exponent (bf16 / fp16)
+    double *scratch;           // one nb x nb binary64 tile per CTA (POTRF)
+    int32_t precision;
+    int32_t fmt;
+    uint64_t timeout_ns;
+};
+
+struct MixedSmem {
+    uint8_t stages[kTcStages][kStageBytes];
+    TcShared ts;
+};
+static_assert(sizeof(SimtSmem<double>) <= sizeof(MixedSmem::stages), "SIMT scratch must fit in the stage area");
+
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float pow2f(int e) { return ldexpf(1.0f, e); }
+
+// CTA-wide max of |x| over a tile of nb*nb floats
+__device__ float tile_absmax(const float *T, int64_t count, float *red) {
+    float m = 0.f;
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) m = fmaxf(m, fabsf(__ldcg(T + i)));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < blockDim.x / 32 ? red[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) red[0] = m;
+    }
+    __syncthreads();
+    const float r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// exponent e with max * 2^e in [2^14, 2^15) (0 for an all-zero tile), clamped
+__device__ __forceinline__ int scale_exponent(float mx) {
+    if (!(mx > 0.f) || !isfinite(mx)) return 0;
+    int E;
+    frexpf(mx, &E);  // mx = f * 2^E, f in [0.5, 1)
+    int e = 15 - E;
+    return e < -126 ? -126 : (e > 126 ? 126 : e);
+}
+
+// Write the tensor-core operand copies of tile t (binary32 values in T).
+__device__ void write_operands(const MixedArgs &g, int64_t t, const float *T, float *red) {
+    const int nb = g.S.nb;
+    const int64_t cnt = (int64_t)nb * nb;
+    const size_t off = (size_t)t * cnt;
+    if (g.fmt == OP_TF32) {
+        uint32_t *hi = reinterpret_cast<uint32_t *>(g.op_hi) + off;
+        uint32_t *lo = g.op_lo ? reinterpret_cast<uint32_t *>(g.op_lo) + off : nullptr;
+        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+            const float x = __ldcg(T + i);
+            const uint32_t h = f32_to_tf32(x);
+            hi[i] = h;
+            if (lo) lo[i] = f32_to_tf32(x - __uint_as_float(h));
+        }
+    } else {
+        const int e = scale_exponent(tile_absmax(T, cnt, red));
+        const float s = pow2f(e);
+        if (threadIdx.x == 0) g.exps[t] = e;
+        if (g.fmt == OP_BF16) {
+            __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(g.op_hi) + off;
+            for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) o[i] = __float2bfloat16_rn(__ldcg(T + i) * s);
+        } else {
+            __half *o = reinterpret_cast<__half *>(g.op_hi) + off;
+            for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) o[i] = __float2half_rn(__ldcg(T + i) * s);
+        }
+    }
+    fence_proxy_async_global();  // make the generic-proxy writes visible to later TMA reads
+    __syncthreads();
+}
+
+struct MixedBody {
+    using Args = MixedArgs;
+    using Smem = MixedSmem;
+    static constexpr bool kSolveTask = false;
+    static constexpr size_t kSmemBytes = sizeof(MixedSmem);
+    static __device__ __forceinline__ void cta_init(const Args &, Smem &sm) { tc_cta_init(sm.ts); }
+    static __device__ __forceinline__ void cta_fini(const Args &, Smem &sm) { tc_cta_fini(sm.ts); }
+    static __device__ __forceinline__ int tiles(const Args &g, int) { return g.S.M; }
+    static __device__ __forceinline__ int64_t task_base(const Args &, int) { return 0; }
+
+    static __device__ void run(const Args &g, const SchedArgs &a, int m, int I, int K, int J, Smem &sm) {
+        const int type = task_type(I, K, J);
+        uint64_t t0 = 0;
+        if (a.trace && threadIdx.x == 0) t0 = global_ns();
+        const int nb = g.S.nb;
+        if (!(a.flags & CHOL_FLAG_NOOP)) {
+            switch (type) {
+            case T_POTRF: {
+                // widen to binary64, factor, round back
+                double *D = g.scratch + (size_t)blockIdx.x * nb * nb;
+                float *T = g.S.tile(J, J);
+                const int64_t cnt = (int64_t)nb * nb;
+                for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) D[i] = (double)__ldcg(T + i);
+                __syncthreads();
+                SimtSmem<double> &ss = *reinterpret_cast<SimtSmem<double> *>(sm.stages);
+                const int li = tile_potrf<double>(D, nb, ss);
+                for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) T[i] = (float)D[i];
+                __syncthreads();
+                if (li && threadIdx.x == 0) {
+                    report_info(a.ctl, (int64_t)J * nb + li);
+                    st_release_s32(&a.ctl->abort, 1);
+                }
+            } break;
+            case T_TRSM: {
+                SimtSmem<float> &ss = *reinterpret_cast<SimtSmem<float> *>(sm.stages);
+                float *B = g.S.tile(I, J);
+                tile_trsm<float>(B, g.S.tile(J, J), nb, ss);
+                write_operands(g, tile_index(I, J), B, reinterpret_cast<float *>(sm.stages));
+            } break;
+            default: {
+                // SYRK (K == I) or GEMM: C(I,K) -= A(I,J) A(K,J)^T on the tensor cores
+                const int64_t ta = tile_index(I, J), tb = tile_index(K, J);
+                float sa = 1.f, sb = 1.f;
+                if (g.fmt != OP_TF32) {
+                    sa = pow2f(-__ldcg(g.exps + ta));
+                    sb = pow2f(-__ldcg(g.exps + tb));
+                }
+                TcGemmArgs ga;
+                const bool three = g.precision == CHOL_FP32;
+                ga.passes = three ? 3 : 1;
+                ga.tf32 = g.fmt == OP_TF32;
+                for (int p = 0; p < 3; ++p) {
+                    ga.mapA[p] = (three && p == 2) ? &g.map_lo : &g.map_hi;
+                    ga.mapB[p] = (three && p == 1) ? &g.map_lo : &g.map_hi;
+                }
+                ga.idesc = make_idesc((uint32_t)g.fmt, 128, nb >= 256 ? 256 : 128);
+                const bool ok = tc_tile_update(sm.ts, &sm.stages[0][0], ga, g.S.tile(I, K), nb, (int)(ta * nb),
+                                               (int)(tb * nb), sa, sb, type == T_SYRK, g.timeout_ns);
+                if (!ok && threadIdx.x == 0) {
+                    if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 3;
+                    st_release_s32(&a.ctl->abort, 1);
+                }
+            } break;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) task_done_bookkeeping(a, type, m, I, K, J, t0);
+    }
+    static __device__ void solve(const Args &, const SchedArgs &, int, Smem &) {}
+};
+
+// ------------------------------------------------------------------ refinement kernels
+// R = B - A X for symmetric A given by its lower triangle (column-major, lda):
+// one CTA per (64-row block, 16-column slice), FP64.
+__global__ void __launch_bounds__(256) residual_kernel(const double *A, int64_t lda, int64_t n, const double *X,
+                                                       int64_t ldx, const double *B, int64_t ldb, double *R,
+                                                       int64_t ldr, int64_t nrhs) {
+    __shared__ double As[kSB][kSB + 1];
+    __shared__ double Xs[kSB][kRC + 1];
+    const int I = blockIdx.x, nblk = (int)((n + kSB - 1) / kSB);
+    const int64_t c0 = (int64_t)blockIdx.y * kRC;
+    const int c = threadIdx.x % kRC, rq = threadIdx.x / kRC;
+    double acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = (int64_t)I * kSB + rq + 16 * q;
+        acc[q] = (i < n && c0 + c < nrhs) ? B[(c0 + c) * ldb + i] : 0.0;
+    }
+    for (int J = 0; J < nblk; ++J) {
+        // As[r][k] = Asym(I*64 + r, J*64 + k)
+        for (int e = threadIdx.x; e < kSB * kSB; e += blockDim.x) {
+            int r, k;
+            if (J <= I) { r = e % kSB; k = e / kSB; }   // read lower block (I, J): rows contiguous
+            else { k = e % kSB; r = e / kSB; }          // read lower block (J, I): its rows are our columns
+            const int64_t i = (int64_t)I * kSB + r, j = (int64_t)J * kSB + k;
+            double v = 0.0;
+            if (i < n && j < n) v = i >= j ? A[j * lda + i] : A[i * lda + j];
+            As[r][k] = v;
+        }
+        for (int e = threadIdx.x; e < kSB * kRC; e += blockDim.x) {
+            const int k = e / kRC, cc = e % kRC;
+            const int64_t j = (int64_t)J * kSB + k;
+            Xs[k][cc] = (j < n && c0 + cc < nrhs) ? X[(c0 + cc) * ldx + j] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < kSB; ++k) {
+            const double xk = Xs[k][c];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[q] = fma(-As[rq + 16 * q][k], xk, acc[q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = (int64_t)I * kSB + rq + 16 * q;
+        if (i < n && c0 + c < nrhs) R[(c0 + c) * ldr + i] = acc[q];
+    }
+}
+
+// ||A||_inf of the symmetric matrix: row sums of |A|, one thread per row.
+__global__ void anorm_rows_kernel(const double *A, int64_t lda, int64_t n, double *rows) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int64_t j = 0; j <= i; ++j) s += fabs(A[j * lda + i]);      // lower part of row i
+    for (int64_t j = i + 1; j < n; ++j) s += fabs(A[i * lda + j]);  // column i below the diagonal
+    rows[i] = s;
+}
+
+// per column: max |R|, max |X|, max |B| (non-negative doubles order like their bits)
+__global__ void colmax_kernel(const double *R, int64_t ldr, const double *X, int64_t ldx, const double *B,
+                              int64_t ldb, int64_t n, int64_t nrhs, unsigned long long *out) {
+    const int64_t c = blockIdx.y;
+    double mr = 0, mx = 0, mb = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        mr = fmax(mr, fabs(R[c * ldr + i]));
+        mx = fmax(mx, fabs(X[c * ldx + i]));
+        mb = fmax(mb, fabs(B[c * ldb + i]));
+    }
+    atomicMax(out + 3 * c + 0, (unsigned long long)__double_as_longlong(mr));
+    atomicMax(out + 3 * c + 1, (unsigned long long)__double_as_longlong(mx));
+    atomicMax(out + 3 * c + 2, (unsigned long long)__double_as_longlong(mb));
+}
+
+__global__ void to_f32_kernel(const double *R, int64_t ldr, float *D, int64_t n, int64_t nrhs) {
+    const int64_t c = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        D[c * n + i] = (float)R[c * ldr + i];
+}
+
+__global__ void axpy_kernel(double *X, int64_t ldx, const float *D, int64_t n, int64_t nrhs) {
+    const int64_t c = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        X[c * ldx + i] += (double)D[c * n + i];
+}
+
+__global__ void max_kernel(const double *v, int64_t n, unsigned long long *out) {
+    double m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, v[i]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+}  // namespace chol
+
+// ------------------------------------------------------------------ handle
+struct chol_factor_s {
+    int64_t n = 0, nb = 0, M = 0;
+    const double *A = nullptr;  // caller's FP64 matrix (referenced)
+    int64_t lda = 0;
+    float *store = nullptr;     // binary32 factor tiles
+    chol_opts opts{};
+    double anorm = -1.0;        // ||A||_inf, computed on first solve
+};
+
+using namespace chol;
+
+static size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static int mixed_factor_impl(int64_t n, const double *A, int64_t lda, const chol_opts &o, chol_factor_s *h,
+                             int64_t *info, chol_stats *stats) {
+    const int64_t nb = o.nb > 0 ? o.nb : chol_default_nb(n, o.precision);
+    CHOL_CHECK_ARG(nb >= 128 && nb <= 1024 && nb % 128 == 0, "mixed precision needs nb in {128, 256, ..., 1024}");
+    const int64_t M = (n + nb - 1) / nb;
+    CHOL_CHECK_ARG(M < 65536 && num_tiles(M) * nb < (1ll << 31), "matrix too large for the operand maps");
+    const int sched = o.schedule == CHOL_SCHED_AUTO ? CHOL_SCHED_DATAFLOW : o.schedule;
+    CHOL_CHECK_ARG(sched >= CHOL_SCHED_FORK_JOIN && sched <= CHOL_SCHED_DATAFLOW, "unknown schedule");
+    cudaStream_t st = (cudaStream_t)o.stream;
+    prepare_pool();
+    const int fmt = op_fmt(o.precision);
+    const int64_t tiles = num_tiles(M);
+    const size_t tile_elems = (size_t)nb * nb;
+    const int grid = df_grid<MixedBody>(o.num_ctas);
+    const int64_t ntasks = num_tasks(M);
+
+    const size_t b_store = a256(tiles * tile_elems * 4);
+    const size_t b_hi = a256(tiles * tile_elems * (fmt == OP_TF32 ? 4 : 2));
+    const size_t b_lo = o.precision == CHOL_FP32 ? a256(tiles * tile_elems * 4) : 0;
+    const size_t b_exp = a256(tiles * 4);
+    const int scr_ctas = grid > 1 ? grid : 1;
+    const size_t b_scr = a256((size_t)scr_ctas * tile_elems * 8);
+    const size_t b_ctl = a256(sizeof(Control));
+    const size_t b_q = sched == CHOL_SCHED_DATAFLOW ? a256((size_t)2 * ntasks * 8) : 0;
+    const size_t b_d = sched == CHOL_SCHED_DATAFLOW ? a256((size_t)ntasks * 4) : 0;
+
+    float *store = nullptr;
+    void *ws = nullptr;
+    CHOL_CUDA(cudaMallocAsync((void **)&store, b_store, st));
+    if (cudaMallocAsync(&ws, b_hi + b_lo + b_exp + b_scr + b_ctl + b_q + b_d, st) != cudaSuccess) {
+        cudaFreeAsync(store, st);
+        set_error("device allocation of the mixed-precision workspace failed");
+        return CHOL_ERR_NOMEM;
+    }
+    char *p = (char *)ws;
+    MixedArgs g;
+    memset(&g, 0, sizeof(g));
+    g.S = TileStore<float>{store, (int32_t)nb, (int32_t)M};
+    g.op_hi = p;
+    g.op_lo = b_lo ? (float *)(p + b_hi) : nullptr;
+    g.exps = (int32_t *)(p + b_hi + b_lo);
+    g.scratch = (double *)(p + b_hi + b_lo + b_exp);
+    Control *ctl = (Control *)(p + b_hi + b_lo + b_exp + b_scr);
+    unsigned long long *queue = (unsigned long long *)(p + b_hi + b_lo + b_exp + b_scr + b_ctl);
+    int32_t *deps = (int32_t *)(p + b_hi + b_lo + b_exp + b_scr + b_ctl + b_q);
+    g.precision = o.precision;
+    g.fmt = fmt;
+    g.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
+
+    int rc = make_operand_map(&g.map_hi, g.op_hi, fmt, tiles * nb, nb);
+    if (rc == CHOL_OK) rc = make_operand_map(&g.map_lo, g.op_lo ? (void *)g.op_lo : g.op_hi, OP_TF32 == fmt ? OP_TF32 : fmt,
+                                             tiles * nb, nb);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    Control hc{};
+    int launches = 0;
+    if (rc == CHOL_OK) do {
+        if ((rc = launch_repack<double, float>(A, lda, n, store, (int)nb, M, st)) != CHOL_OK) break;
+        if (cudaMemsetAsync(ctl, 0, sizeof(Control), st) != cudaSuccess ||
+            cudaMemsetAsync(g.exps, 0, tiles * 4, st) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "memset", __FILE__, __LINE__);
+            break;
+        }
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "event", __FILE__, __LINE__);
+            break;
+        }
+        SchedArgs a{ctl, o.trace, o.trace_capacity, o.flags, 0};
+        if (sched == CHOL_SCHED_DATAFLOW) {
+            DFArgs d{};
+            d.queue = queue;
+            d.deps = deps;
+            d.capacity = ntasks;
+            d.total = ntasks;
+            d.num_matrices = 1;
+            chol_opts oo = o;
+            oo.num_ctas = grid;
+            rc = launch_dataflow<MixedBody>(g, a, d, oo, st, &launches, e0);
+        } else {
+            cudaEventRecord(e0, st);
+            rc = run_fork_join<MixedBody>(g, a, (int)M, sched == CHOL_SCHED_FORK_JOIN_NAIVE, st, &launches);
+        }
+        if (rc != CHOL_OK) break;
+        cudaEventRecord(e1, st);
+        if (cudaMemcpyAsync(&hc, ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "mixed factor", __FILE__, __LINE__);
+            break;
+        }
+    } while (0);
+    cudaFreeAsync(ws, st);
+    if (rc == CHOL_OK && hc.status) {
+        set_error("mixed factorization: device-side wait expired (site %d)", hc.timeout_where);
+        rc = hc.status;
+    }
+    if (rc != CHOL_OK) {
+        cudaFreeAsync(store, st);
+    } else {
+        *info = hc.info;
+        h->n = n;
+        h->nb = nb;
+        h->M = M;
+        h->A = A;
+        h->lda = lda;
+        h->store = store;
+        h->opts = o;
+        if (stats) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            for (int i = 0; i < 4; ++i) stats->tasks[i] = (int64_t)hc.tasks[i];
+            stats->nb = nb;
+            stats->schedule = sched;
+            stats->launches = launches;
+            stats->trace_records = (int64_t)hc.trace_count;
+            stats->device_ms = ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
+}
+
+static thread_local chol_stats g_mixed_stats;
+
+extern "C" {
+
+int chol_mixed_factor(int64_t n, const double *A, int64_t lda, const chol_opts *opts, chol_factor_h *out,
+                      int64_t *info) {
+    CHOL_CHECK_ARG(out != nullptr && info != nullptr, "out or info is NULL");
+    *out = nullptr;
+    *info = 0;
+    CHOL_CHECK_ARG(n >= 1, "n < 1");
+    CHOL_CHECK_ARG(lda >= n, "lda < n");
+    CHOL_CHECK_ARG(A != nullptr, "A is NULL");
+    chol_opts o = resolve_opts(opts);
+    CHOL_CHECK_ARG(o.precision >= CHOL_FP32 && o.precision <= CHOL_FP16, "precision must be FP32, TF32, BF16 or FP16");
+    chol_factor_s *h = new chol_factor_s();
+    memset(&g_mixed_stats, 0, sizeof(g_mixed_stats));
+    const int rc = mixed_factor_impl(n, A, lda, o, h, info, &g_mixed_stats);
+    if (rc != CHOL_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return CHOL_OK;
+}
+
+// statistics of the last chol_mixed_factor on this thread
+int chol_mixed_last_stats(chol_stats *st) {
+    CHOL_CHECK_ARG(st != nullptr, "stats is NULL");
+    *st = g_mixed_stats;
+    return CHOL_OK;
+}
+
+int chol_mixed_get_factor(chol_factor_h h, double *L, int64_t ldl) {
+    if (!h || !h->store) {
+        set_error("invalid factor handle");
+        return CHOL_ERR_HANDLE;
+    }
+    CHOL_CHECK_ARG(L != nullptr && ldl >= h->n, "L is NULL or ldl < n");
+    cudaStream_t st = (cudaStream_t)h->opts.stream;
+    int rc = launch_unpack<float, double>(h->store, (int)h->nb, h->M, L, ldl, h->n, st);
+    if (rc != CHOL_OK) return rc;
+    CHOL_CUDA(cudaStreamSynchronize(st));
+    return CHOL_OK;
+}
+
+int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                     int32_t *iters_out, double *berr_out) {
+    if (!h || !h->store) {
+        set_error("invalid factor handle");
+        return CHOL_ERR_HANDLE;
+    }
+    const int64_t n = h->n;
+    CHOL_CHECK_ARG(nrhs >= 1 && B && X && ldb >= n && ldx >= n, "bad B / X arguments");
+    const chol_opts &o = h->opts;
+    cudaStream_t st = (cudaStream_t)o.stream;
+    prepare_pool();
+    const size_t b_r = a256((size_t)n * nrhs * 8), b_d = a256((size_t)n * nrhs * 4);
+    const size_t b_max = a256((size_t)3 * nrhs * 8 + 8), b_rows = a256((size_t)n * 8);
+    const size_t b_sws = a256(solve_ws_bytes(n, nrhs));
+    void *ws = nullptr;
+    CHOL_CUDA(cudaMallocAsync(&ws, b_r + b_d + b_max + b_rows + b_sws, st));
+    char *p = (char *)ws;
+    double *R = (double *)p;
+    float *D = (float *)(p + b_r);
+    unsigned long long *mx = (unsigned long long *)(p + b_r + b_d);
+    double *rows = (double *)(p + b_r + b_d + b_max);
+    void *sws = p + b_r + b_d + b_max + b_rows;
+    const int nblk = (int)((n + kSB - 1) / kSB), ny = (int)((nrhs + kRC - 1) / kRC);
+    const dim3 vgrid((unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), (unsigned)nrhs);
+    int rc = CHOL_OK;
+    std::vector<unsigned long long> hm(3 * nrhs + 1);
+    int it = 0;
+    double berr = 1.0;
+    do {
+        if (h->anorm < 0) {
+            anorm_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h->A, h->lda, n, rows);
+            if (cudaMemsetAsync(mx + 3 * nrhs, 0, 8, st) != cudaSuccess) { rc = CHOL_ERR_CUDA; break; }
+            max_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(rows, n, mx + 3 * nrhs);
+            unsigned long long v = 0;
+            if (cudaMemcpyAsync(&v, mx + 3 * nrhs, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "anorm", __FILE__, __LINE__);
+                break;
+            }
+            memcpy(&h->anorm, &v, 8);
+        }
+        if (cudaMemset2DAsync(X, ldx * 8, 0, n * 8, nrhs, st) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "zero X", __FILE__, __LINE__);
+            break;
+        }
+        for (it = 0;; ++it) {
+            // r = b - A x (FP64) and the backward error
+            residual_kernel<<<dim3(nblk, ny), 256, 0, st>>>(h->A, h->lda, n, X, ldx, B, ldb, R, n, nrhs);
+            if (cudaMemsetAsync(mx, 0, 3 * nrhs * 8, st) != cudaSuccess) { rc = CHOL_ERR_CUDA; break; }
+            colmax_kernel<<<vgrid, 256, 0, st>>>(R, n, X, ldx, B, ldb, n, nrhs, mx);
+            if (cudaMemcpyAsync(hm.data(), mx, 3 * nrhs * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "refinement", __FILE__, __LINE__);
+                break;
+            }
+            berr = 0.0;
+            for (int64_t c = 0; c < nrhs; ++c) {
+                double r, x, b;
+                memcpy(&r, &hm[3 * c], 8);
+                memcpy(&x, &hm[3 * c + 1], 8);
+                memcpy(&b, &hm[3 * c + 2], 8);
+                const double den = h->anorm * x + b;
+                const double e = den > 0 ? r / den : r;
+                berr = e > berr ? e : berr;
+            }
+            if (berr <= o.refine_tol || it >= o.max_iter || !(berr == berr)) break;
+            // d = L^-T L^-1 r in binary32 on the tile store; x += d
+            to_f32_kernel<<<vgrid, 256, 0, st>>>(R, n, D, n, nrhs);
+            rc = launch_solve<float, TileMajorL<float>>(TileMajorL<float>{h->store, h->nb}, D, n, n, nrhs, sws,
+                                                        o.timeout_s, st);
+            if (rc != CHOL_OK) break;
+            axpy_kernel<<<vgrid, 256, 0, st>>>(X, ldx, D, n, nrhs);
+        }
+        if (rc == CHOL_OK && cudaGetLastError() != cudaSuccess) rc = CHOL_ERR_CUDA;
+        if (rc == CHOL_OK) {
+            int32_t sst = 0;
+            if (cudaMemcpyAsync(&sst, sws, 4, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                cudaStreamSynchronize(st) == cudaSuccess && sst != 0) {
+                set_error("refinement solve: device-side wait expired");
+                rc = sst;
+            }
+        }
+    } while (0);
+    cudaFreeAsync(ws, st);
+    if (iters_out) *iters_out = it;
+    if (berr_out) *berr_out = berr;
+    if (rc == CHOL_OK && !(berr <= o.refine_tol)) {
+        set_error("refinement stopped at backward error %.3e after %d iterations", berr, it);
+        rc = CHOL_ERR_NOT_CONVERGED;
+    }
+    return rc;
+}
+
+void chol_factor_free(chol_factor_h h) {
+    if (!h) return;
+    if (h->store) cudaFreeAsync(h->store, (cudaStream_t)h->opts.stream);
+    h->store = nullptr;
+    delete h;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ test hook: one tcgen05 tile update
+namespace chol {
+
+struct TcTestArgs {
+    CUtensorMap map_hi;
+    CUtensorMap map_lo;
+    float *C;
+    int32_t nb, precision, fmt, eA, eB, lower;
+    int32_t *ok;
+};
+
+__global__ void __launch_bounds__(256) tc_test_kernel(const __grid_constant__ TcTestArgs g) {
+    extern __shared__ uint8_t dyn[];
+    MixedSmem &sm = *reinterpret_cast<MixedSmem *>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
+    tc_cta_init(sm.ts);
+    TcGemmArgs ga;
+    const bool three = g.precision == CHOL_FP32;
+    ga.passes = three ? 3 : 1;
+    ga.tf32 = g.fmt == OP_TF32;
+    for (int p = 0; p < 3; ++p) {
+        ga.mapA[p] = (three && p == 2) ? &g.map_lo : &g.map_hi;
+        ga.mapB[p] = (three && p == 1) ? &g.map_lo : &g.map_hi;
+    }
+    ga.idesc = make_idesc((uint32_t)g.fmt, 128, g.nb >= 256 ? 256 : 128);
+    // two updates in a row exercise the barrier phases across tasks
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep)
+        ok = tc_tile_update(sm.ts, &sm.stages[0][0], ga, g.C + (size_t)rep * g.nb * g.nb, g.nb, 0, g.nb,
+                            ldexpf(1.f, -g.eA), ldexpf(1.f, -g.eB), g.lower != 0, 2000000000ull);
+    if (threadIdx.x == 0) *g.ok = ok ? 1 : 0;
+    tc_cta_fini(sm.ts);
+}
+
+}  // namespace chol
+
+extern "C" {
+
+// C[0] and C[1] (two nb x nb FP32 tiles, row-major, contiguous) each receive
+// C -= 2^-eA 2^-eB * sum_p A_p B_p^T with operands from `ops`: rows [0, nb) of
+// each operand array are A, rows [nb, 2 nb) are B; `ops` holds the hi array
+// and, for CHOL_FP32, the lo array right after it.  Returns CHOL_OK, or
+// CHOL_ERR_TIMEOUT if a wait expired.
+int chol_test_tc_update(int32_t precision, int64_t nb, const void *ops, int32_t eA, int32_t eB, float *C,
+                        int32_t lower) {
+    CHOL_CHECK_ARG(precision >= CHOL_FP32 && precision <= CHOL_FP16, "precision");
+    CHOL_CHECK_ARG(nb >= 128 && nb <= 1024 && nb % 128 == 0, "nb");
+    CHOL_CHECK_ARG(ops && C, "NULL pointer");
+    TcTestArgs g;
+    memset(&g, 0, sizeof(g));
+    g.fmt = op_fmt(precision);
+    const size_t eb = g.fmt == OP_TF32 ? 4 : 2;
+    int rc = make_operand_map(&g.map_hi, (void *)ops, g.fmt, 2 * nb, nb);
+    if (rc == CHOL_OK && precision == CHOL_FP32)
+        rc = make_operand_map(&g.map_lo, (char *)ops + 2 * nb * nb * eb, g.fmt, 2 * nb, nb);
+    else if (rc == CHOL_OK)
+        g.map_lo = g.map_hi;
+    if (rc != CHOL_OK) return rc;
+    g.C = C;
+    g.nb = (int32_t)nb;
+    g.precision = precision;
+    g.eA = eA;
+    g.eB = eB;
+    g.lower = lower;
+    int32_t *dok = nullptr;
+    CHOL_CUDA(cudaMalloc(&dok, 4));
+    const size_t smem = sizeof(MixedSmem) + 1024;
+    CHOL_CUDA(cudaFuncSetAttribute(tc_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    g.ok = dok;
+    tc_test_kernel<<<1, 256, smem>>>(g);
+    int32_t ok = 0;
+    cudaError_t e = cudaMemcpy(&ok, dok, 4, cudaMemcpyDeviceToHost);
+    cudaFree(dok);
+    if (e != cudaSuccess) return cuda_fail(e, "tc test", __FILE__, __LINE__);
+    if (!ok) {
+        set_error("tcgen05 tile update: wait expired");
+        return CHOL_ERR_TIMEOUT;
+    }
+    return CHOL_OK;
+}
+
+}  // extern "C"

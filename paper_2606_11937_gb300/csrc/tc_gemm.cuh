@@ -1,0 +1,335 @@
+// tc_gemm.cuh -- SYRK/GEMM tile updates on the 5th-generation tensor cores
+// (tcgen05) for the mixed-precision factorization:
+//
+//     C (FP32 tile, row-major nb x nb)  -=  scale * sum_p A_p B_p^T
+//
+// where A_p, B_p are low-precision copies (bf16, fp16 or tf32-rounded fp32)
+// of two panel tiles A_IJ, A_KJ written by the TRSM epilogue, and p runs over
+// one product (BF16, FP16, TF32) or three (FP32 = hi*hi + hi*lo + lo*hi).
+//
+// Operands are staged by TMA (cp.async.bulk.tensor, 128-byte swizzle, K-major)
+// into a ring of shared-memory stages, one thread issues tcgen05.mma with the
+// FP32 accumulator in tensor memory (M = 128 rows per MMA, N = min(nb, 256)),
+// and four epilogue warps read the accumulator with tcgen05.ld and update C.
+// Every mbarrier wait is bounded by a %globaltimer deadline; an expired wait
+// raises the CTA's abort flag and the roles unwind.
+#pragma once
+
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace chol {
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for the completion of the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, uint64_t deadline) {
+    while (!mbar_test(b, parity)) {
+        if (global_ns() > deadline) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint64_t *bar, int32_t x,
+                                            int32_t y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(dst), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T ; kind f16 (bf16 / fp16 operands) or tf32
+template <bool TF32>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    if (TF32)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+}
+// 32 TMEM lanes (one per thread of the warp) x 32 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes in 8-row (1024-byte) groups; the buffer is 1024-byte aligned.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                     // descriptor version
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulate, A/B format (0 fp16, 1 bf16, 2 tf32),
+// both K-major, M x N.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// ------------------------------------------------------------------ configuration
+constexpr int kTcStages = 3;
+constexpr int kBoxRows = 128;              // rows per TMA box
+constexpr int kBoxBytes = kBoxRows * 128;  // 128 bytes of K per row
+constexpr int kStageBytes = 4 * kBoxBytes; // up to 2 A boxes + 2 B boxes
+
+// Operand formats of the mixed precisions
+enum OpFmt : int32_t { OP_F16 = 0, OP_BF16 = 1, OP_TF32 = 2 };
+
+struct TcShared {
+    uint64_t full[kTcStages];
+    uint64_t empty[kTcStages];
+    uint64_t acc_full;
+    uint64_t tmem_empty;
+    uint64_t drain;
+    uint32_t tmem_base;
+    uint32_t ring;       // stage fills issued (== consumed) before the current task
+    uint32_t acc_uses;   // accumulator uses completed before the current task
+    uint32_t drains;     // drain barrier completions
+    int32_t fail;        // an mbarrier wait expired in this CTA
+};
+
+struct TcGemmArgs {
+    const CUtensorMap *mapA[3];  // per product p: map of the A operand
+    const CUtensorMap *mapB[3];
+    int32_t passes;              // products per update (1 or 3)
+    int32_t tf32;                // kind::tf32 (else kind::f16)
+    uint32_t idesc;
+};
+
+// One CTA (256 threads) initialises its barriers and allocates 512 TMEM columns.
+__device__ inline void tc_cta_init(TcShared &ts) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&ts.full[s], 1);
+            mbar_init(&ts.empty[s], 1);
+        }
+        mbar_init(&ts.acc_full, 1);
+        mbar_init(&ts.tmem_empty, 4);
+        mbar_init(&ts.drain, 1);
+        ts.ring = 0;
+        ts.acc_uses = 0;
+        ts.drains = 0;
+        ts.fail = 0;
+        mbar_fence_init();
+    }
+    if (threadIdx.x / 32 == 1) {
+        tmem_alloc(&ts.tmem_base, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+// Wait (bounded) for every MMA this CTA issued, then free the TMEM columns.
+__device__ inline void tc_cta_fini(TcShared &ts) {
+    __syncthreads();
+    if (threadIdx.x == 32) {
+        tc_commit(&ts.drain);
+        mbar_wait(&ts.drain, ts.drains & 1, global_ns() + 2000000000ull);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x / 32 == 1) tmem_dealloc(ts.tmem_base, 512);
+}
+
+__device__ __forceinline__ int tc_failed(const TcShared &ts) { return *(volatile const int32_t *)&ts.fail; }
+
+// C[nb x nb] -= sa * sb * sum_p A_p B_p^T (sa, sb powers of two, applied one
+// after the other so their product never underflows on its own), A rows
+// starting at row aRow0 of the operand maps, B rows at bRow0.  lower: skip
+// sub-tiles strictly above the diagonal (SYRK).  Called by all 256 threads;
+// returns false if a wait expired.
+__device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, const TcGemmArgs &g, float *C, int nb,
+                                      int aRow0, int bRow0, float sa, float sb, bool lower, uint64_t timeout_ns) {
+    const int MH = nb >= 256 ? 2 : 1;          // 128-row halves per sub-tile
+    const int NN = nb >= 256 ? 256 : 128;      // MMA N
+    const int SR = MH * 128;                   // sub-tile rows
+    const int nsr = nb / SR, nsc = nb / NN;
+    const int kchunks = nb / (g.tf32 ? 32 : 64);
+    const uint32_t stage_bytes = (uint32_t)(MH + NN / 128) * kBoxBytes;
+    const uint32_t ring0 = ts.ring, acc0 = ts.acc_uses;
+    const uint64_t deadline = global_ns() + timeout_ns;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    auto skip = [&](int ri, int ci) { return lower && ci * NN >= (ri + 1) * SR; };
+    int nsub = 0;
+    for (int ri = 0; ri < nsr; ++ri)
+        for (int ci = 0; ci < nsc; ++ci) nsub += skip(ri, ci) ? 0 : 1;
+    const uint32_t iters_per_sub = (uint32_t)(g.passes * kchunks);
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        fence_proxy_async_global();
+        uint32_t f = ring0;
+        for (int ri = 0; ri < nsr && !tc_failed(ts); ++ri)
+            for (int ci = 0; ci < nsc && !tc_failed(ts); ++ci) {
+                if (skip(ri, ci)) continue;
+                for (int p = 0; p < g.passes && !tc_failed(ts); ++p)
+                    for (int kc = 0; kc < kchunks; ++kc, ++f) {
+                        const int s = (int)(f % kTcStages);
+                        if (f >= (uint32_t)kTcStages &&
+                            !mbar_wait(&ts.empty[s], ((f / kTcStages) & 1) ^ 1, deadline)) {
+                            *(volatile int32_t *)&ts.fail = 1;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&ts.full[s], stage_bytes);
+                        const uint32_t dst = smem_u32(stages + (size_t)s * kStageBytes);
+                        const int x = kc * (g.tf32 ? 32 : 64);
+                        for (int h = 0; h < MH; ++h)
+                            tma_load_2d(dst + h * kBoxBytes, g.mapA[p], &ts.full[s], x, aRow0 + ri * SR + h * 128);
+                        for (int q = 0; q < NN / 128; ++q)
+                            tma_load_2d(dst + (MH + q) * kBoxBytes, g.mapB[p], &ts.full[s], x,
+                                        bRow0 + ci * NN + q * 128);
+                    }
+            }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        uint32_t f = ring0, u = acc0;
+        for (int ri = 0; ri < nsr && !tc_failed(ts); ++ri)
+            for (int ci = 0; ci < nsc && !tc_failed(ts); ++ci) {
+                if (skip(ri, ci)) continue;
+                if (u > 0 && !mbar_wait(&ts.tmem_empty, (u - 1) & 1, deadline)) {
+                    *(volatile int32_t *)&ts.fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                bool first = true;
+                for (int p = 0; p < g.passes && !tc_failed(ts); ++p)
+                    for (int kc = 0; kc < kchunks; ++kc, ++f) {
+                        const int s = (int)(f % kTcStages);
+                        if (!mbar_wait(&ts.full[s], (f / kTcStages) & 1, deadline)) {
+                            *(volatile int32_t *)&ts.fail = 1;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t base = smem_u32(stages + (size_t)s * kStageBytes);
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            const uint64_t bdesc = sdesc_sw128(base + MH * kBoxBytes + k4 * 32);
+                            for (int h = 0; h < MH; ++h) {
+                                const uint64_t adesc = sdesc_sw128(base + h * kBoxBytes + k4 * 32);
+                                const uint32_t d = ts.tmem_base + (uint32_t)(h * NN);
+                                if (g.tf32) tc_mma<true>(d, adesc, bdesc, g.idesc, first ? 0u : 1u);
+                                else tc_mma<false>(d, adesc, bdesc, g.idesc, first ? 0u : 1u);
+                            }
+                            first = false;
+                        }
+                        tc_commit(&ts.empty[s]);
+                    }
+                tc_commit(&ts.acc_full);
+                ++u;
+            }
+    } else if (warp >= 4) {
+        // ---------------- epilogue: TMEM -> registers -> C
+        const int q = warp - 4;  // TMEM lane quadrant of this warp
+        uint32_t u = acc0;
+        for (int ri = 0; ri < nsr; ++ri)
+            for (int ci = 0; ci < nsc; ++ci) {
+                if (skip(ri, ci)) continue;
+                if (!mbar_wait(&ts.acc_full, u & 1, deadline)) {
+                    *(volatile int32_t *)&ts.fail = 1;
+                    ri = nsr;
+                    break;
+                }
+                tc_fence_after();
+                for (int h = 0; h < MH; ++h) {
+                    const int row = ri * SR + h * 128 + q * 32 + lane;
+                    float *crow = C + (size_t)row * nb + ci * NN;
+                    for (int c = 0; c < NN; c += 32) {
+                        uint32_t r[32];
+                        tmem_ld32(ts.tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * NN + c), r);
+                        tmem_ld_wait();
+                        float4 *cv = reinterpret_cast<float4 *>(crow + c);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float4 v = __ldcg(cv + j);
+                            v.x -= (__uint_as_float(r[4 * j + 0]) * sa) * sb;
+                            v.y -= (__uint_as_float(r[4 * j + 1]) * sa) * sb;
+                            v.z -= (__uint_as_float(r[4 * j + 2]) * sa) * sb;
+                            v.w -= (__uint_as_float(r[4 * j + 3]) * sa) * sb;
+                            cv[j] = v;
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ts.tmem_empty);
+                ++u;
+            }
+    }
+    __syncthreads();
+    const bool ok = !tc_failed(ts);
+    __syncthreads();
+    if (threadIdx.x == 0 && ok) {
+        ts.ring = ring0 + (uint32_t)nsub * iters_per_sub;
+        ts.acc_uses = acc0 + (uint32_t)nsub;
+    }
+    __syncthreads();
+    return ok;
+}
+
+}  // namespace chol
