@@ -30,6 +30,7 @@ def mixed(A, prec, sched="dataflow", nb=128, **kw):
 
     import paper_2606_11937_gb300 as chol
     dA = chol.colmajor(A)
+    kw.setdefault("timeout_s", 20.0)
     rc, h = chol.chol_mixed_factor(dA, chol.opts(precision=prec, schedule=sched, nb=nb, **kw), raise_on_error=False)
     torch.cuda.synchronize()
     return rc, h, dA
