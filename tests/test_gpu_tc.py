@@ -63,7 +63,7 @@ def test_tc_tile_update(prec, nb, lower):
     for a, b in pairs:
         want = np.stack([oracle.tile_op("gemm", a * s, b, want[r]) for r in range(2)])
         absum += np.abs(a) @ np.abs(b).T * s
-    tol = (2 * nb + 8) * 2.0 ** -24 * absum + 2.0 ** -23 * np.abs(C.astype(np.float64))
+    tol = [(2 * nb + 8) * 2.0 ** -24 * absum + 2.0 ** -23 * np.abs(C[r].astype(np.float64)) for r in range(2)]
     mask = np.ones((nb, nb), dtype=bool)
     if lower and nb >= 512:
         SR, NN = 256, 256   # sub-tiles strictly above the diagonal are skipped
@@ -73,5 +73,5 @@ def test_tc_tile_update(prec, nb, lower):
                     mask[ri * SR:(ri + 1) * SR, ci * NN:(ci + 1) * NN] = False
     for r in range(2):
         err = np.abs(got[r] - want[r])
-        assert np.all(err[mask] <= tol[mask]), (prec, nb, float(np.max(err[mask] / tol[mask])))
+        assert np.all(err[mask] <= tol[r][mask]), (prec, nb, float(np.max(err[mask] / tol[r][mask])))
         assert np.array_equal(got[r][~mask], C[r].astype(np.float64)[~mask])
