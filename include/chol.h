@@ -166,6 +166,28 @@ int chol_solve(int64_t n, int64_t nrhs, const double *L, double *B);
 int chol_solve_ex(int64_t n, int64_t nrhs, const double *L, int64_t ldl,
                   double *B, int64_t ldb, const chol_opts *opts);
 
+/* The same FP64 solve as chol_solve_ex, for callers that cannot allocate
+ * device memory: an application whose own memory manager has reserved the
+ * GPU's memory, or a latency-critical loop that must not pay the
+ * device-wide synchronization cudaMalloc / cudaFree can cause.  (The paper
+ * has no counterpart; this is an interface of this library only.)
+ *   - allocates nothing: its scratch is a fixed 4 MiB array in device memory
+ *     that every GPU loading the library holds until the process exits;
+ *   - the first call on a device looks up that array's device address (once
+ *     per device, with that device current); make the first call before any
+ *     stream capture;
+ *   - sizes whose scratch exceeds 4 MiB (2 * ceil(n/64) * ceil(nrhs/16) flags
+ *     of 4 bytes plus a 32 KiB control block) return CHOL_ERR_ARG with a
+ *     message; use chol_solve_ex for those;
+ *   - all calls share the one array and clear what they use at the start, so
+ *     calls that overlap on the GPU (different streams, threads or devices'
+ *     streams on the same device) race and must be serialized by the caller;
+ *   - L: n x n lower factor (ldl >= n), B: n x nrhs (ldb >= n), device,
+ *     column-major; B is overwritten with the solution; stream: cudaStream_t
+ *     (NULL = legacy default stream); returns after the solve completed. */
+int chol_solve_noalloc(int64_t n, int64_t nrhs, const double *L, int64_t ldl,
+                       double *B, int64_t ldb, void *stream);
+
 /* --------------------------------------------- mixed precision + refinement */
 
 typedef struct chol_factor_s *chol_factor_h;

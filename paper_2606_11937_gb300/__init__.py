@@ -78,6 +78,7 @@ SIGNATURES = {
     "chol_factor_host": (ctypes.c_int, [_i64, _vp, _i64, _P(chol_opts), _P(_i64), _P(chol_stats)]),
     "chol_solve": (ctypes.c_int, [_i64, _i64, _vp, _vp]),
     "chol_solve_ex": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _i64, _P(chol_opts)]),
+    "chol_solve_noalloc": (ctypes.c_int, [_i64, _i64, _vp, _i64, _vp, _i64, _vp]),
     "chol_mixed_factor": (ctypes.c_int, [_i64, _vp, _i64, _P(chol_opts), _P(_vp), _P(_i64)]),
     "chol_mixed_solve": (ctypes.c_int, [_vp, _i64, _vp, _i64, _vp, _i64, _P(_i32), _P(_dbl)]),
     "chol_mixed_get_factor": (ctypes.c_int, [_vp, _vp, _i64]),
@@ -251,6 +252,14 @@ def chol_solve_ex(L, B, o: chol_opts | None = None, n: int | None = None, nrhs: 
     if raise_on_error:
         _check(rc, "chol_solve_ex")
     return rc
+
+
+def chol_solve_noalloc(L, B, n: int | None = None, nrhs: int | None = None, stream=None) -> int:
+    """Allocation-free FP64 solve (see include/chol.h): returns the status."""
+    n = L.shape[0] if n is None else n
+    nrhs = (B.shape[1] if B.dim() == 2 else 1) if nrhs is None else nrhs
+    st = _stream() if stream is None else int(stream)
+    return lib().chol_solve_noalloc(int(n), int(nrhs), _ptr(L), _ld(L), _ptr(B), _ld(B), st)
 
 
 class MixedFactor:

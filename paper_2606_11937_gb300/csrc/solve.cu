@@ -2,10 +2,25 @@
 // backward substitution (the use the paper motivates in Section 1).
 #include <string.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "solve_impl.cuh"
 
 using namespace chol;
+
+// ------------------------------------------------------------------ allocation-free solve
+// Scratch of chol_solve_noalloc: the solve's control block (tickets, status)
+// and its per-block ready flags, in device memory that exists as soon as the
+// library is loaded on a device (every device that loads the library keeps
+// these 4 MiB until the process exits).  Host code cannot use the symbol's
+// name as a device address; the address is looked up once per device.
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[256] = {};
+}  // namespace
 
 extern "C" {
 
@@ -38,6 +53,48 @@ int chol_solve_ex(int64_t n, int64_t nrhs, const double *L, int64_t ldl, double 
 
 int chol_solve(int64_t n, int64_t nrhs, const double *L, double *B) {
     return chol_solve_ex(n, nrhs, L, n > 1 ? n : 1, B, n > 1 ? n : 1, nullptr);
+}
+
+int chol_solve_noalloc(int64_t n, int64_t nrhs, const double *L, int64_t ldl, double *B, int64_t ldb,
+                       void *stream) {
+    CHOL_CHECK_ARG(n >= 0 && nrhs >= 0, "n < 0 or nrhs < 0");
+    CHOL_CHECK_ARG(ldl >= (n > 1 ? n : 1) && ldb >= (n > 1 ? n : 1), "ldl or ldb < max(1, n)");
+    if (n == 0 || nrhs == 0) return CHOL_OK;
+    CHOL_CHECK_ARG(L != nullptr && B != nullptr, "L or B is NULL");
+    const size_t need = solve_ws_bytes(n, nrhs);
+    if (need > kNoAllocScratchBytes) {
+        set_error("argument: chol_solve_noalloc needs %zu bytes of scratch for n=%lld, nrhs=%lld; its fixed "
+                  "scratch holds %zu bytes (use chol_solve_ex)",
+                  need, (long long)n, (long long)nrhs, kNoAllocScratchBytes);
+        return CHOL_ERR_ARG;
+    }
+    int dev = 0;
+    CHOL_CUDA(cudaGetDevice(&dev));
+    CHOL_CHECK_ARG(dev >= 0 && dev < 256, "device ordinal out of range");
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            // first call on this device: look up the device address of the array
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+            g_noalloc_addr[dev] = p;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // launch_solve clears the control block and flags it uses before the sweeps
+    int rc = launch_solve<double, ColMajorL<double>>(ColMajorL<double>{L, ldl}, B, ldb, n, nrhs, scratch, 60.0, st);
+    if (rc != CHOL_OK) return rc;
+    int32_t h[2] = {0, 0};
+    CHOL_CUDA(cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CHOL_CUDA(cudaStreamSynchronize(st));
+    if (h[0]) {
+        set_error("solve: device-side wait expired (site %d)", h[1]);
+        return h[0];
+    }
+    return CHOL_OK;
 }
 
 }  // extern "C"
