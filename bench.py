@@ -48,7 +48,10 @@ def parse():
     p.add_argument("--n", type=int, default=32768)
     p.add_argument("--nb", type=int, default=0)
     p.add_argument("--schedule", default="dataflow")
-    p.add_argument("--workload", default="fp64", choices=["fp64", "mixed", "batched", "serve"])
+    p.add_argument("--workload", default="fp64", choices=["fp64", "mixed", "batched", "serve", "sweep"])
+    p.add_argument("--sweep-nb", default="")
+    p.add_argument("--sweep-sched", default="")
+    p.add_argument("--noop", action="store_true")
     p.add_argument("--precision", default="fp32")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")

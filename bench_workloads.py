@@ -1,0 +1,148 @@
+"""Further bench.py workloads (``--workload mixed|batched|serve|sweep``).
+
+Each prints one JSON line with the keys of the default FP64 line.
+
+* mixed: mixed-precision factorization (trailing SYRK/GEMM on tcgen05) of
+  the SE covariance (n, nugget 1e-2), then a solve of 16 N(0, 1) right-hand
+  sides with FP64 iterative refinement to backward error 1e-14.  value =
+  factorization TFLOP/s (n^3/3); the line also carries the refinement
+  iterations, the backward error and the time to solution.
+* sweep: FP64 factorization time for every tile order x schedule (the
+  paper's tile-size sweep, Section 4.1, on the GPU); one line per point.
+"""
+from __future__ import annotations
+
+import json
+import statistics
+import time
+
+import bench
+
+
+def _common(args, world, value, unit, ms, config, dtype, extra):
+    line = {"metric": bench.METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+    line.update(extra)
+    return line
+
+
+def run_mixed(args, world, rank, local):
+    import torch
+
+    import paper_2606_11937_gb300 as chol
+    import seeded_inputs as si
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    prec = args.precision
+    nb = args.nb or chol.chol_default_nb(n, prec)
+    A = si.se_covariance_torch(n, seed=1, lengthscale=0.1, nugget=1e-2, device=dev).T
+    g = torch.Generator(device=dev)
+    g.manual_seed(2)
+    B = torch.randn((16, n), dtype=torch.float64, device=dev, generator=g).T  # column-major n x 16
+    stream = torch.cuda.current_stream(dev)
+    o = chol.opts(precision=prec, schedule=args.schedule, nb=nb, stream=stream.cuda_stream, max_iter=50)
+    flops = n ** 3 / 3.0
+
+    def step():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, h = chol.chol_mixed_factor(A, o)
+        e1.record(stream)
+        e1.synchronize()
+        st = chol.chol_mixed_last_stats()
+        return e0.elapsed_time(e1), st, h
+
+    for _ in range(args.warmup):
+        _, _, h = step()
+        h.close()
+    torch.cuda.synchronize()
+    bench.barrier(world)
+    times, kms = [], []
+    with bench.ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            ms, st, h = step()
+            times.append(ms)
+            kms.append(st.device_ms)
+            if len(times) < args.steps:
+                h.close()
+    torch.cuda.synchronize()
+    bench.barrier(world)
+    # solve with refinement using the last factor
+    t = time.perf_counter()
+    rc, X, iters, berr = h.solve(B, raise_on_error=False)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t
+    h.close()
+    ms = bench.allreduce_max(statistics.mean(times), world)
+    value = world * flops / (ms / 1e3) / 1e12
+    achieved = flops / (statistics.mean(kms) / 1e3) / 1e12
+    peaks = bench.measured_peaks()
+    bf16 = peaks.get("bf16_tflops", 1873.4)
+    peak = {"bf16": bf16, "fp16": bf16, "tf32": bf16 / 2, "fp32": bf16 / 2 / 3}[prec]
+    if rank == 0:
+        line = _common(args, world, value, "TFLOP/s", ms,
+                       {"workload": f"mixed-precision ({prec} trailing update) tiled Cholesky n={n} nb={nb} "
+                                    f"{args.schedule}, SE covariance (l=0.1, nugget 1e-2, seed 1), then solve of 16 "
+                                    f"N(0,1) RHS with FP64 refinement to 1e-14",
+                        "n": n, "nb": nb, "precision": prec, "schedule": args.schedule,
+                        "l2": f"inputs larger than L2 ({n * n * 8 / 1e9:.1f} GB FP64 matrix)"},
+                       "f32", {"roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                            "frac": achieved / peak, "traffic": None,
+                                            "kernel": "df_kernel<MixedBody> (whole schedule)",
+                                            "peak_source": f"measured bf16 {bf16} TFLOP/s x nominal ratio for {prec}"},
+                               "refinement": {"status": rc, "iterations": iters, "berr": berr,
+                                              "solve_s": solve_s, "time_to_solution_s": ms / 1e3 + solve_s},
+                               "clocks": clk.summary()})
+        print(json.dumps(line), flush=True)
+
+
+def run_sweep(args, world, rank, local):
+    """Tile order x schedule sweep of the FP64 factorization (Section 4.1 on the GPU)."""
+    import torch
+
+    import paper_2606_11937_gb300 as chol
+    import seeded_inputs as si
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    A0 = si.se_covariance_torch(n, seed=1, lengthscale=0.1, nugget=1e-2, device=dev).T
+    A = torch.empty_strided((n, n), (1, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    nbs = [int(x) for x in (args.sweep_nb or "64,128,256,512").split(",")]
+    scheds = (args.sweep_sched or "dataflow,fork_join,fork_join_naive").split(",")
+    for nb in nbs:
+        for sched in scheds:
+            for flags in ([0, chol.CHOL_FLAG_NOOP] if args.noop else [0]):
+                o = chol.opts(schedule=sched, nb=nb, flags=flags, stream=stream.cuda_stream)
+                ts = []
+                for _ in range(max(1, args.steps)):
+                    A.copy_(A0)
+                    torch.cuda.synchronize()
+                    rc, info, st = chol.chol_factor_ex(A, o)
+                    ts.append(st.device_ms)
+                ms = statistics.median(ts)
+                tasks = sum(st.tasks)
+                rec = {"workload": "sweep", "n": n, "nb": nb, "schedule": sched, "noop": bool(flags),
+                       "ms": ms, "tflops": (n ** 3 / 3) / (ms / 1e3) / 1e12 if not flags else None,
+                       "tasks": tasks, "us_per_task": 1e3 * ms / tasks, "launches": st.launches}
+                if rank == 0:
+                    print(json.dumps(rec), flush=True)
+
+
+def run(args, world, rank, local):
+    if args.workload == "mixed":
+        return run_mixed(args, world, rank, local)
+    if args.workload == "sweep":
+        return run_sweep(args, world, rank, local)
+    if args.workload == "batched":
+        import bench_batched
+        return bench_batched.run_batched(args, world, rank, local)
+    if args.workload == "serve":
+        import bench_batched
+        return bench_batched.run_serve(args, world, rank, local)
+    raise ValueError(args.workload)
