@@ -52,6 +52,12 @@ def parse():
     p.add_argument("--sweep-nb", default="")
     p.add_argument("--sweep-sched", default="")
     p.add_argument("--noop", action="store_true")
+    p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--serve-requests", type=int, default=120)
+    p.add_argument("--serve-rates", default="20,80,320")
+    p.add_argument("--serve-nmax", type=int, default=8192)
+    p.add_argument("--serve-slots", type=int, default=4)
+    p.add_argument("--serve-budget-gb", type=float, default=64.0)
     p.add_argument("--precision", default="fp32")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
@@ -83,7 +89,8 @@ def allreduce_max(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 

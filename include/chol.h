@@ -227,7 +227,8 @@ int chol_mixed_last_stats(chol_stats *stats);
 typedef struct chol_batch_s *chol_batch_h;
 
 /* Plan a batched factor + solve of `batch` independent SPD systems of orders
- * n[i] (host array), 1 right-hand side each, in one persistent kernel launch
+ * n[i] (host array, 1 <= n[i] <= 2048, batch <= 65535), 1 right-hand side
+ * each, in one persistent kernel launch
  * that is captured once into a CUDA graph and replayed by chol_batch_run.
  * precision: CHOL_FP64 or CHOL_FP32 (true binary32 arithmetic).  The tile
  * order of each matrix comes from the autotuner's table for its n (opts->nb

@@ -323,3 +323,116 @@ def chol_mixed_factor(A, o: chol_opts | None = None, raise_on_error: bool = True
     if raise_on_error:
         _check(rc, "chol_mixed_factor")
     return rc, (MixedFactor(h.value, int(info.value), A) if rc == CHOL_OK else None)
+
+
+class BatchPlan:
+    """Handle of chol_batch_plan (one persistent launch in a CUDA graph)."""
+
+    def __init__(self, ns, o: chol_opts | None = None):
+        self.ns = [int(x) for x in ns]
+        arr = (_i64 * len(self.ns))(*self.ns)
+        h = _vp(None)
+        o = o or opts()
+        _check(lib().chol_batch_plan(len(self.ns), arr, ctypes.byref(o), ctypes.byref(h)), "chol_batch_plan")
+        self.h = h.value
+
+    def run(self, As, Bs):
+        """As: column-major CUDA tensors (overwritten by L), Bs: CUDA vectors
+        (overwritten by the solutions).  Returns the list of info values."""
+        k = len(self.ns)
+        pa = (_vp * k)(*[_ptr(a) for a in As])
+        lda = (_i64 * k)(*[_ld(a) for a in As])
+        pb = (_vp * k)(*[_ptr(b) for b in Bs])
+        info = (_i64 * k)()
+        _check(lib().chol_batch_run(self.h, pa, lda, pb, info), "chol_batch_run")
+        return list(info)
+
+    def stats(self) -> chol_stats:
+        st = chol_stats()
+        _check(lib().chol_batch_stats(self.h, ctypes.byref(st)), "chol_batch_stats")
+        return st
+
+    def close(self):
+        if self.h:
+            lib().chol_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def chol_batch_plan(ns, o: chol_opts | None = None) -> BatchPlan:
+    return BatchPlan(ns, o)
+
+
+def chol_autotune(n: int, precision="fp64", cache_path: str | None = None, budget_s: float = 5.0) -> chol_opts:
+    """Measured (nb, schedule) for order n; returns a chol_opts with them set."""
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o = chol_opts()
+    _check(lib().chol_autotune(int(n), p, cache_path.encode() if cache_path else None, float(budget_s),
+                               ctypes.byref(o)), "chol_autotune")
+    return o
+
+
+def _res_dict(r: chol_result) -> dict:
+    return {f: getattr(r, f) for f, _ in chol_result._fields_}
+
+
+class Server:
+    """Handle of chol_server_create (continuous-batching solve server)."""
+
+    def __init__(self, budget_bytes: int, slots: int = 4, o: chol_opts | None = None):
+        h = _vp(None)
+        o = o or opts()
+        _check(lib().chol_server_create(int(budget_bytes), int(slots), ctypes.byref(o), ctypes.byref(h)),
+               "chol_server_create")
+        self.h = h.value
+
+    def submit(self, B, X, A=None, factor_id: int = 0, precision="fp64", n: int | None = None) -> int:
+        r = chol_request()
+        r.n = int(n if n is not None else B.shape[0])
+        r.A = _ptr(A) or None
+        r.lda = _ld(A) if A is not None else 0
+        r.factor_id = int(factor_id)
+        r.B = _ptr(B)
+        r.ldb = _ld(B)
+        r.X = _ptr(X)
+        r.ldx = _ld(X)
+        r.nrhs = B.shape[1] if B.dim() == 2 else 1
+        r.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        t = ctypes.c_uint64(0)
+        _check(lib().chol_server_submit(self.h, ctypes.byref(r), ctypes.byref(t)), "chol_server_submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        r = chol_result()
+        rc = lib().chol_server_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(r))
+        return rc, (_res_dict(r) if rc == CHOL_OK else None)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0) -> dict:
+        r = chol_result()
+        _check(lib().chol_server_wait(self.h, ctypes.c_uint64(ticket), ctypes.byref(r), float(timeout_s)),
+               "chol_server_wait")
+        return _res_dict(r)
+
+    def release(self, factor_id: int) -> int:
+        return lib().chol_server_release(self.h, ctypes.c_uint64(factor_id))
+
+    def stats(self) -> dict:
+        s = chol_server_stats_t()
+        _check(lib().chol_server_stats(self.h, ctypes.byref(s)), "chol_server_stats")
+        return {f: getattr(s, f) for f, _ in chol_server_stats_t._fields_}
+
+    def close(self):
+        if self.h:
+            lib().chol_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -30,29 +30,25 @@ struct FactorWs {
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-static int factor_fp64_device(int64_t n, double *A, int64_t lda, const chol_opts &o, int64_t *info,
-                              chol_stats *stats) {
-    const int64_t nb = o.nb > 0 ? o.nb : chol_default_nb(n, CHOL_FP64);
-    CHOL_CHECK_ARG(nb >= 1 && nb <= 2048, "nb must be in [1, 2048]");
+// Repack A into `store` (tile order nb), run the schedule, optionally unpack
+// the factor into A_out, read back the control block and synchronize.
+static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o, double *store, int64_t nb,
+                     int64_t *info, chol_stats *stats, double *A_out, int64_t lda_out) {
     const int64_t M = (n + nb - 1) / nb;
-    CHOL_CHECK_ARG(M < 65536, "too many tiles per dimension (n / nb must be < 65536)");
-    int sched = o.schedule == CHOL_SCHED_AUTO ? CHOL_SCHED_DATAFLOW : o.schedule;
+    const int sched = o.schedule == CHOL_SCHED_AUTO ? CHOL_SCHED_DATAFLOW : o.schedule;
     CHOL_CHECK_ARG(sched >= CHOL_SCHED_FORK_JOIN && sched <= CHOL_SCHED_DATAFLOW, "unknown schedule");
     cudaStream_t st = (cudaStream_t)o.stream;
-    prepare_pool();
-
     const int64_t ntasks = num_tasks(M);
-    const size_t store_bytes = align256((size_t)num_tiles(M) * nb * nb * sizeof(double));
     const size_t ctl_bytes = align256(sizeof(Control));
     const size_t q_bytes = sched == CHOL_SCHED_DATAFLOW ? align256((size_t)2 * ntasks * 8) : 0;
     const size_t d_bytes = sched == CHOL_SCHED_DATAFLOW ? align256((size_t)ntasks * 4) : 0;
     FactorWs ws;
-    CHOL_CUDA(cudaMallocAsync(&ws.base, store_bytes + ctl_bytes + q_bytes + d_bytes, st));
+    CHOL_CUDA(cudaMallocAsync(&ws.base, ctl_bytes + q_bytes + d_bytes, st));
     char *p = (char *)ws.base;
-    ws.store = (double *)p;
-    ws.ctl = (Control *)(p + store_bytes);
-    ws.queue = (unsigned long long *)(p + store_bytes + ctl_bytes);
-    ws.deps = (int32_t *)(p + store_bytes + ctl_bytes + q_bytes);
+    ws.store = store;
+    ws.ctl = (Control *)p;
+    ws.queue = (unsigned long long *)(p + ctl_bytes);
+    ws.deps = (int32_t *)(p + ctl_bytes + q_bytes);
 
     int rc = CHOL_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -72,7 +68,7 @@ static int factor_fp64_device(int64_t n, double *A, int64_t lda, const chol_opts
         }
         if (rc != CHOL_OK) break;
         cudaEventRecord(e1, st);
-        if ((rc = launch_unpack<double, double>(ws.store, (int)nb, M, A, lda, n, st)) != CHOL_OK) break;
+        if (A_out && (rc = launch_unpack<double, double>(ws.store, (int)nb, M, A_out, lda_out, n, st)) != CHOL_OK) break;
         if (cudaMemcpyAsync(&h, ws.ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "readback", __FILE__, __LINE__); break; }
         if (cudaStreamSynchronize(st) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "sync", __FILE__, __LINE__); break; }
     } while (0);
@@ -85,7 +81,7 @@ static int factor_fp64_device(int64_t n, double *A, int64_t lda, const chol_opts
             for (int i = 0; i < 4; ++i) stats->tasks[i] = (int64_t)h.tasks[i];
             stats->nb = nb;
             stats->schedule = sched;
-            stats->launches = launches;
+            stats->launches = launches + (A_out ? 2 : 1);
             stats->trace_records = (int64_t)h.trace_count;
             stats->device_ms = ms;
         }
@@ -97,6 +93,48 @@ static int factor_fp64_device(int64_t n, double *A, int64_t lda, const chol_opts
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     return rc;
+}
+
+static int64_t resolve_nb(int64_t n, const chol_opts &o) { return o.nb > 0 ? o.nb : chol_default_nb(n, CHOL_FP64); }
+
+size_t fp64_store_bytes(int64_t n, int64_t nb) {
+    const int64_t M = (n + nb - 1) / nb;
+    return align256((size_t)num_tiles(M) * nb * nb * sizeof(double));
+}
+
+static int factor_fp64_device(int64_t n, double *A, int64_t lda, const chol_opts &o, int64_t *info,
+                              chol_stats *stats) {
+    const int64_t nb = resolve_nb(n, o);
+    CHOL_CHECK_ARG(nb >= 1 && nb <= 2048, "nb must be in [1, 2048]");
+    CHOL_CHECK_ARG((n + nb - 1) / nb < 65536, "too many tiles per dimension (n / nb must be < 65536)");
+    cudaStream_t st = (cudaStream_t)o.stream;
+    prepare_pool();
+    double *store = nullptr;
+    CHOL_CUDA(cudaMallocAsync((void **)&store, fp64_store_bytes(n, nb), st));
+    const int rc = fp64_core(n, A, lda, o, store, nb, info, stats, A, lda);
+    cudaFreeAsync(store, st);
+    return rc;
+}
+
+// Factor into a tile store that the caller keeps (freed with cudaFreeAsync);
+// used by the server for resident factors.
+int fp64_factor_store(int64_t n, const double *A, int64_t lda, const chol_opts &o, double **store_out,
+                      int64_t *nb_out, int64_t *info) {
+    *store_out = nullptr;
+    const int64_t nb = resolve_nb(n, o);
+    CHOL_CHECK_ARG(nb >= 1 && nb <= 2048 && (n + nb - 1) / nb < 65536, "bad tile order");
+    cudaStream_t st = (cudaStream_t)o.stream;
+    prepare_pool();
+    double *store = nullptr;
+    CHOL_CUDA(cudaMallocAsync((void **)&store, fp64_store_bytes(n, nb), st));
+    const int rc = fp64_core(n, A, lda, o, store, nb, info, nullptr, nullptr, 0);
+    if (rc != CHOL_OK) {
+        cudaFreeAsync(store, st);
+        return rc;
+    }
+    *store_out = store;
+    *nb_out = nb;
+    return CHOL_OK;
 }
 
 }  // namespace chol

@@ -22,6 +22,31 @@ std::mutex g_noalloc_mu;
 void *g_noalloc_addr[256] = {};
 }  // namespace
 
+namespace chol {
+
+// X <- A^{-1} X with the factor held in a row-major FP64 tile store (server).
+int fp64_solve_store(const double *store, int64_t n, int64_t nb, double *X, int64_t ldx, int64_t nrhs,
+                     cudaStream_t st, double timeout_s) {
+    void *ws = nullptr;
+    CHOL_CUDA(cudaMallocAsync(&ws, solve_ws_bytes(n, nrhs), st));
+    int rc = launch_solve<double, TileMajorL<double>>(TileMajorL<double>{store, nb}, X, ldx, n, nrhs, ws, timeout_s,
+                                                      st);
+    int32_t h[2] = {0, 0};
+    if (rc == CHOL_OK) {
+        if (cudaMemcpyAsync(h, ws, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            rc = cuda_fail(cudaGetLastError(), "solve readback", __FILE__, __LINE__);
+        else if (h[0]) {
+            set_error("solve: device-side wait expired (site %d)", h[1]);
+            rc = h[0];
+        }
+    }
+    cudaFreeAsync(ws, st);
+    return rc;
+}
+
+}  // namespace chol
+
 extern "C" {
 
 int chol_solve_ex(int64_t n, int64_t nrhs, const double *L, int64_t ldl, double *B, int64_t ldb,
