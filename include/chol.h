@@ -110,7 +110,8 @@ typedef struct {
     double refine_tol;      /* refinement target backward error (default 1e-14) */
     double timeout_s;       /* bound on any device-side wait (default 60 s) */
     void *stream;           /* cudaStream_t; NULL = legacy default stream */
-    int32_t num_ctas;       /* dataflow grid size; 0 = one per SM */
+    int32_t num_ctas;       /* dataflow grid size; 0 = default (4 CTAs per SM for the CUDA-core
+                               bodies, 1 per SM for the tensor-core body) */
     int32_t reserved;
     chol_trace_rec *trace;  /* device buffer of trace_capacity records, or NULL */
     int64_t trace_capacity;

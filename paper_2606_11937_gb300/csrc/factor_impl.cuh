@@ -9,6 +9,7 @@
 //   static __device__ int64_t task_base(const Args &, int m);   // offset of m's task ids
 //   static __device__ void run(const Args &, const SchedArgs &, int m, int I, int K, int J, Smem &);
 //   static constexpr bool kSolveTask;  // a SOLVE task follows POTRF(M-1) of every matrix
+//   static constexpr int kCtasPerSm;   // default persistent CTAs per SM
 //   static __device__ void solve(const Args &, const SchedArgs &, int m, Smem &);
 #pragma once
 
@@ -164,6 +165,7 @@ struct SimtBody {
     };
     using Smem = SimtSmem<T>;
     static constexpr bool kSolveTask = false;
+    static constexpr int kCtasPerSm = 4;  // DFMA latency is hidden by several task CTAs per SM
     static constexpr size_t kSmemBytes = sizeof(SimtSmem<T>);
     static __device__ __forceinline__ void cta_init(const Args &, Smem &) {}
     static __device__ __forceinline__ void cta_fini(const Args &, Smem &) {}
@@ -423,7 +425,7 @@ int df_grid(int num_ctas) {
         occ = 1;
     const int sms = num_sms();
     const int maxg = sms * occ;
-    if (num_ctas <= 0) return sms;
+    if (num_ctas <= 0) return sms * (occ < Body::kCtasPerSm ? occ : Body::kCtasPerSm);
     return num_ctas < maxg ? num_ctas : maxg;
 }
 
