@@ -87,8 +87,11 @@ enum {
     CHOL_FLAG_NOOP = 1,          /* replace every tile kernel body by a no-op (Section 4.2 overhead runs) */
     CHOL_FLAG_PRIORITY = 2,      /* dataflow: POTRF/TRSM/SYRK before GEMM (OpenMP 4.5 priorities analog) */
     CHOL_FLAG_GRAPH = 4,         /* fork-join: replay the per-step launches from a cached CUDA graph */
-    CHOL_FLAG_TEST_WITHHOLD = 8  /* dataflow test hook: never release the last POTRF, so the
+    CHOL_FLAG_TEST_WITHHOLD = 8, /* dataflow test hook: never release the last POTRF, so the
                                     bounded waits must expire with CHOL_ERR_TIMEOUT */
+    CHOL_FLAG_FP64_TC = 16       /* FP64: run SYRK/GEMM on the bf16 tensor cores with binary64
+                                    accuracy (exact 8 x 7-bit slicing of row-scaled values, 36
+                                    integer-exact products per update); tiles of order 128 */
 };
 
 /* One trace record per executed task (written when opts->trace != NULL). */

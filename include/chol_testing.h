@@ -28,6 +28,15 @@ extern "C" {
 int chol_test_tc_update(int32_t precision, int64_t nb, const void *ops, int32_t eA, int32_t eB, float *C,
                         int32_t lower);
 
+/* One binary64-accurate tensor-core tile update (the CHOL_FLAG_FP64_TC GEMM,
+ * Section 3.1 GEMM formula), run twice by one CTA after the operands are
+ * split into bf16 slices on the device:
+ *     C[r] <- C[r] - A B^T,   r = 0, 1
+ * A, B: 128 x 128 row-major binary64 tiles; C: two contiguous 128 x 128
+ * row-major binary64 tiles; all device pointers.  Returns CHOL_OK,
+ * CHOL_ERR_CUDA or CHOL_ERR_TIMEOUT. */
+int chol_test_ozaki_update(const double *A, const double *B, double *C);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ CHOL_OK, CHOL_ERR_ARG, CHOL_ERR_NOT_SPD, CHOL_ERR_NOMEM, CHOL_ERR_CUDA = 0, -1, 
 CHOL_ERR_TIMEOUT, CHOL_ERR_NOT_CONVERGED, CHOL_ERR_BUSY, CHOL_ERR_HANDLE, CHOL_ERR_UNSUPPORTED = -5, -6, -7, -8, -9
 CHOL_FP64, CHOL_FP32, CHOL_TF32, CHOL_BF16, CHOL_FP16 = 0, 1, 2, 3, 4
 CHOL_SCHED_AUTO, CHOL_SCHED_FORK_JOIN, CHOL_SCHED_FORK_JOIN_NAIVE, CHOL_SCHED_DATAFLOW = 0, 1, 2, 3
-CHOL_FLAG_NOOP, CHOL_FLAG_PRIORITY, CHOL_FLAG_GRAPH, CHOL_FLAG_TEST_WITHHOLD = 1, 2, 4, 8
+CHOL_FLAG_NOOP, CHOL_FLAG_PRIORITY, CHOL_FLAG_GRAPH, CHOL_FLAG_TEST_WITHHOLD, CHOL_FLAG_FP64_TC = 1, 2, 4, 8, 16
 
 PRECISIONS = {"fp64": CHOL_FP64, "fp32": CHOL_FP32, "tf32": CHOL_TF32, "bf16": CHOL_BF16, "fp16": CHOL_FP16}
 SCHEDULES = {"auto": CHOL_SCHED_AUTO, "fork_join": CHOL_SCHED_FORK_JOIN,
@@ -85,6 +85,7 @@ SIGNATURES = {
     "chol_factor_free": (None, [_vp]),
     "chol_mixed_last_stats": (ctypes.c_int, [_P(chol_stats)]),
     "chol_test_tc_update": (ctypes.c_int, [_i32, _i64, _vp, _i32, _i32, _vp, _i32]),
+    "chol_test_ozaki_update": (ctypes.c_int, [_vp, _vp, _vp]),
     "chol_batch_plan": (ctypes.c_int, [_i32, _P(_i64), _P(chol_opts), _P(_vp)]),
     "chol_batch_run": (ctypes.c_int, [_vp, _P(_vp), _P(_i64), _P(_vp), _P(_i64)]),
     "chol_batch_stats": (ctypes.c_int, [_vp, _P(chol_stats)]),

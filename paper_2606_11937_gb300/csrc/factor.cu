@@ -19,6 +19,9 @@ namespace chol {
 
 template struct TileStore<double>;
 
+int fp64tc_schedule(double *store, int64_t n, Control *ctl, unsigned long long *queue, int32_t *deps, int sched,
+                    const chol_opts &o, cudaStream_t st, int *launches, cudaEvent_t e0);
+
 // Allocation layout of one FP64 factorization.
 struct FactorWs {
     void *base = nullptr;
@@ -60,7 +63,9 @@ static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "event", __FILE__, __LINE__); break; }
         TileStore<double> S{ws.store, (int32_t)nb, (int32_t)M};
         SchedArgs a{ws.ctl, o.trace, o.trace_capacity, o.flags, 0};
-        if (sched == CHOL_SCHED_DATAFLOW) {
+        if (o.flags & CHOL_FLAG_FP64_TC) {
+            rc = fp64tc_schedule(ws.store, n, ws.ctl, ws.queue, ws.deps, sched, o, st, &launches, e0);
+        } else if (sched == CHOL_SCHED_DATAFLOW) {
             rc = run_dataflow<double>(S, a, ws.queue, ws.deps, o, st, &launches, e0);
         } else {
             cudaEventRecord(e0, st);
@@ -95,7 +100,10 @@ static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o
     return rc;
 }
 
-static int64_t resolve_nb(int64_t n, const chol_opts &o) { return o.nb > 0 ? o.nb : chol_default_nb(n, CHOL_FP64); }
+static int64_t resolve_nb(int64_t n, const chol_opts &o) {
+    if (o.flags & CHOL_FLAG_FP64_TC) return 128;  // the tensor-core FP64 body works on 128 x 128 tiles
+    return o.nb > 0 ? o.nb : chol_default_nb(n, CHOL_FP64);
+}
 
 size_t fp64_store_bytes(int64_t n, int64_t nb) {
     const int64_t M = (n + nb - 1) / nb;
@@ -106,6 +114,8 @@ static int factor_fp64_device(int64_t n, double *A, int64_t lda, const chol_opts
                               chol_stats *stats) {
     const int64_t nb = resolve_nb(n, o);
     CHOL_CHECK_ARG(nb >= 1 && nb <= 2048, "nb must be in [1, 2048]");
+    CHOL_CHECK_ARG(!(o.flags & CHOL_FLAG_FP64_TC) || o.nb == 0 || o.nb == 128,
+                   "CHOL_FLAG_FP64_TC works on tiles of order 128 (nb = 0 or 128)");
     CHOL_CHECK_ARG((n + nb - 1) / nb < 65536, "too many tiles per dimension (n / nb must be < 65536)");
     cudaStream_t st = (cudaStream_t)o.stream;
     prepare_pool();

@@ -1,0 +1,193 @@
+// fp64tc.cu -- FP64 factorization whose SYRK/GEMM run on the tensor cores with
+// binary64 accuracy (exact bf16 slicing, ozaki.cuh); POTRF and TRSM stay on
+// the CUDA cores in binary64.  Selected with CHOL_FLAG_FP64_TC; tiles of order
+// 128.  Both schedules of Section 3.2 run this body unchanged.
+#include <cuda.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "factor_impl.cuh"
+#include "ozaki.cuh"
+
+namespace chol {
+
+int make_operand_map(CUtensorMap *map, void *base, int fmt, int64_t rows, int64_t nb, int box_rows);
+
+// 2-D map over the slice store (rows x 128 bf16) with boxes of 64 columns x box_rows.
+static int make_slice_map(CUtensorMap *map, void *base, int64_t rows, int box_rows) {
+    return make_operand_map(map, base, OP_BF16, rows, kOzNb, box_rows);
+}
+
+struct OzArgs {
+    CUtensorMap mapA;   // slice store, 128-row boxes
+    CUtensorMap mapB;   // slice store, 64-row boxes
+    TileStore<double> S;
+    __nv_bfloat16 *slices;  // per tile: 8 slices of 128 x 128
+    int32_t *rexp;          // per tile: 128 row exponents
+    uint64_t timeout_ns;
+};
+
+struct OzBody {
+    using Args = OzArgs;
+    using Smem = OzSmem;
+    static constexpr bool kSolveTask = false;
+    static constexpr int kCtasPerSm = 1;
+    static constexpr size_t kSmemBytes = sizeof(OzSmem);
+    static __device__ __forceinline__ void cta_init(const Args &, Smem &sm) { oz_cta_init(sm.os); }
+    static __device__ __forceinline__ void cta_fini(const Args &, Smem &sm) { oz_cta_fini(sm.os); }
+    static __device__ __forceinline__ int tiles(const Args &g, int) { return g.S.M; }
+    static __device__ __forceinline__ int64_t task_base(const Args &, int) { return 0; }
+
+    static __device__ void run(const Args &g, const SchedArgs &a, int m, int I, int K, int J, Smem &sm) {
+        const int type = task_type(I, K, J);
+        uint64_t t0 = 0;
+        if (a.trace && threadIdx.x == 0) t0 = global_ns();
+        const TileStore<double> &S = g.S;
+        SimtSmem<double> &ss = *reinterpret_cast<SimtSmem<double> *>(sm.B);
+        if (!(a.flags & CHOL_FLAG_NOOP)) {
+            switch (type) {
+            case T_POTRF: {
+                const int li = tile_potrf(S.tile(J, J), kOzNb, ss);
+                if (li && threadIdx.x == 0) {
+                    report_info(a.ctl, (int64_t)J * kOzNb + li);
+                    st_release_s32(&a.ctl->abort, 1);
+                }
+            } break;
+            case T_TRSM: {
+                tile_trsm(S.tile(I, J), S.tile(J, J), kOzNb, ss);
+                const int64_t t = tile_index(I, J);
+                ozaki_split(S.tile(I, J), g.slices + (size_t)t * kOzS * kOzNb * kOzNb, g.rexp + t * kOzNb);
+            } break;
+            default: {
+                const int64_t ta = tile_index(I, J), tb = tile_index(K, J);
+                const bool ok = ozaki_tile_update(sm, &g.mapA, &g.mapB, S.tile(I, K), (int)(ta * kOzS * kOzNb),
+                                                  (int)(tb * kOzS * kOzNb), g.rexp + ta * kOzNb,
+                                                  g.rexp + tb * kOzNb, g.timeout_ns);
+                if (!ok && threadIdx.x == 0) {
+                    if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 4;
+                    st_release_s32(&a.ctl->abort, 1);
+                }
+            } break;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) task_done_bookkeeping(a, type, m, I, K, J, t0);
+    }
+    static __device__ void solve(const Args &, const SchedArgs &, int, Smem &) {}
+};
+
+static size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Workspace bytes beyond the FP64 tile store for an order-n factorization.
+size_t fp64tc_extra_bytes(int64_t n) {
+    const int64_t M = (n + kOzNb - 1) / kOzNb;
+    return a256((size_t)num_tiles(M) * kOzS * kOzNb * kOzNb * 2) + a256((size_t)num_tiles(M) * kOzNb * 4);
+}
+
+// Run the schedule with the tensor-core FP64 body on a repacked tile store.
+int fp64tc_schedule(double *store, int64_t n, Control *ctl, unsigned long long *queue, int32_t *deps, int sched,
+                    const chol_opts &o, cudaStream_t st, int *launches, cudaEvent_t e0) {
+    const int64_t M = (n + kOzNb - 1) / kOzNb;
+    const int64_t tiles = num_tiles(M);
+    const size_t b_sl = a256((size_t)tiles * kOzS * kOzNb * kOzNb * 2);
+    CHOL_CHECK_ARG(tiles * kOzS * kOzNb < (1ll << 31), "matrix too large for the slice maps");
+    void *ws = nullptr;
+    CHOL_CUDA(cudaMallocAsync(&ws, fp64tc_extra_bytes(n), st));
+    OzArgs g;
+    memset(&g, 0, sizeof(g));
+    g.S = TileStore<double>{store, kOzNb, (int32_t)M};
+    g.slices = (__nv_bfloat16 *)ws;
+    g.rexp = (int32_t *)((char *)ws + b_sl);
+    g.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
+    int rc = make_slice_map(&g.mapA, g.slices, tiles * kOzS * kOzNb, 128);
+    if (rc == CHOL_OK) rc = make_slice_map(&g.mapB, g.slices, tiles * kOzS * kOzNb, 64);
+    SchedArgs a{ctl, o.trace, o.trace_capacity, o.flags, 0};
+    if (rc == CHOL_OK) {
+        if (sched == CHOL_SCHED_DATAFLOW) {
+            DFArgs d{};
+            d.queue = queue;
+            d.deps = deps;
+            d.capacity = num_tasks(M);
+            d.total = num_tasks(M);
+            d.num_matrices = 1;
+            rc = launch_dataflow<OzBody>(g, a, d, o, st, launches, e0);
+        } else {
+            if (e0) cudaEventRecord(e0, st);
+            rc = run_fork_join<OzBody>(g, a, (int)M, sched == CHOL_SCHED_FORK_JOIN_NAIVE, st, launches);
+        }
+    }
+    cudaFreeAsync(ws, st);
+    return rc;
+}
+
+// ------------------------------------------------------------------ test hook
+__global__ void __launch_bounds__(256) oz_split_kernel(const double *T, __nv_bfloat16 *slices, int32_t *rexp) {
+    ozaki_split(T + (size_t)blockIdx.x * kOzNb * kOzNb, slices + (size_t)blockIdx.x * kOzS * kOzNb * kOzNb,
+                rexp + blockIdx.x * kOzNb);
+}
+
+struct OzTestArgs {
+    CUtensorMap mapA, mapB;
+    double *C;
+    const int32_t *rexp;
+    int32_t *ok;
+};
+
+__global__ void __launch_bounds__(256) oz_test_kernel(const __grid_constant__ OzTestArgs g) {
+    extern __shared__ uint8_t dyn[];
+    OzSmem &sm = *reinterpret_cast<OzSmem *>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
+    oz_cta_init(sm.os);
+    bool ok = true;
+    // two updates in a row (C[0], C[1]) exercise the barrier phases across tasks
+    for (int rep = 0; rep < 2 && ok; ++rep)
+        ok = ozaki_tile_update(sm, &g.mapA, &g.mapB, g.C + (size_t)rep * kOzNb * kOzNb, 0, kOzS * kOzNb, g.rexp,
+                               g.rexp + kOzNb, 2000000000ull);
+    if (threadIdx.x == 0) *g.ok = ok ? 1 : 0;
+    oz_cta_fini(sm.os);
+}
+
+}  // namespace chol
+
+using namespace chol;
+
+extern "C" {
+
+int chol_test_ozaki_update(const double *A, const double *B, double *C) {
+    CHOL_CHECK_ARG(A && B && C, "NULL pointer");
+    const size_t tile = (size_t)kOzNb * kOzNb;
+    double *T = nullptr;
+    __nv_bfloat16 *sl = nullptr;
+    int32_t *rexp = nullptr, *dok = nullptr;
+    CHOL_CUDA(cudaMalloc(&T, 2 * tile * 8));
+    CHOL_CUDA(cudaMalloc(&sl, 2 * kOzS * tile * 2));
+    CHOL_CUDA(cudaMalloc(&rexp, 2 * kOzNb * 4 + 16));
+    dok = rexp + 2 * kOzNb;
+    CHOL_CUDA(cudaMemcpy(T, A, tile * 8, cudaMemcpyDeviceToDevice));
+    CHOL_CUDA(cudaMemcpy(T + tile, B, tile * 8, cudaMemcpyDeviceToDevice));
+    oz_split_kernel<<<2, 256>>>(T, sl, rexp);
+    OzTestArgs g;
+    memset(&g, 0, sizeof(g));
+    int rc = make_slice_map(&g.mapA, sl, 2 * kOzS * kOzNb, 128);
+    if (rc == CHOL_OK) rc = make_slice_map(&g.mapB, sl, 2 * kOzS * kOzNb, 64);
+    if (rc == CHOL_OK) {
+        g.C = C;
+        g.rexp = rexp;
+        g.ok = dok;
+        const size_t smem = sizeof(OzSmem) + 1024;
+        CHOL_CUDA(cudaFuncSetAttribute(oz_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        oz_test_kernel<<<1, 256, smem>>>(g);
+        int32_t ok = 0;
+        const cudaError_t e = cudaMemcpy(&ok, dok, 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_fail(e, "ozaki test", __FILE__, __LINE__);
+        else if (!ok) {
+            set_error("ozaki tile update: wait expired");
+            rc = CHOL_ERR_TIMEOUT;
+        }
+    }
+    cudaFree(T);
+    cudaFree(sl);
+    cudaFree(rexp);
+    return rc;
+}
+
+}  // extern "C"

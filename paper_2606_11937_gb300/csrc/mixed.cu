@@ -44,8 +44,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // 2-D map over `rows` rows of nb elements (row pitch nb * elem bytes), boxes of
-// 128 bytes of K x 128 rows, 128-byte swizzle.
-int make_operand_map(CUtensorMap *map, void *base, int fmt, int64_t rows, int64_t nb) {
+// 128 bytes of K x box_rows rows, 128-byte swizzle.
+int make_operand_map(CUtensorMap *map, void *base, int fmt, int64_t rows, int64_t nb, int box_rows) {
     auto enc = tensor_map_encoder();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -57,7 +57,7 @@ int make_operand_map(CUtensorMap *map, void *base, int fmt, int64_t rows, int64_
                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     cuuint64_t dims[2] = {(cuuint64_t)nb, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(nb * eb)};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)kBoxRows};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / eb), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     memset(map, 0, sizeof(*map));
     CUresult r = enc(map, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -388,9 +388,8 @@ static int mixed_factor_impl(int64_t n, const double *A, int64_t lda, const chol
     g.fmt = fmt;
     g.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
 
-    int rc = make_operand_map(&g.map_hi, g.op_hi, fmt, tiles * nb, nb);
-    if (rc == CHOL_OK) rc = make_operand_map(&g.map_lo, g.op_lo ? (void *)g.op_lo : g.op_hi, OP_TF32 == fmt ? OP_TF32 : fmt,
-                                             tiles * nb, nb);
+    int rc = make_operand_map(&g.map_hi, g.op_hi, fmt, tiles * nb, nb, kBoxRows);
+    if (rc == CHOL_OK) rc = make_operand_map(&g.map_lo, g.op_lo ? (void *)g.op_lo : g.op_hi, fmt, tiles * nb, nb, kBoxRows);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     Control hc{};
     int launches = 0;
@@ -658,9 +657,9 @@ int chol_test_tc_update(int32_t precision, int64_t nb, const void *ops, int32_t 
     memset(&g, 0, sizeof(g));
     g.fmt = op_fmt(precision);
     const size_t eb = g.fmt == OP_TF32 ? 4 : 2;
-    int rc = make_operand_map(&g.map_hi, (void *)ops, g.fmt, 2 * nb, nb);
+    int rc = make_operand_map(&g.map_hi, (void *)ops, g.fmt, 2 * nb, nb, kBoxRows);
     if (rc == CHOL_OK && precision == CHOL_FP32)
-        rc = make_operand_map(&g.map_lo, (char *)ops + 2 * nb * nb * eb, g.fmt, 2 * nb, nb);
+        rc = make_operand_map(&g.map_lo, (char *)ops + 2 * nb * nb * eb, g.fmt, 2 * nb, nb, kBoxRows);
     else if (rc == CHOL_OK)
         g.map_lo = g.map_hi;
     if (rc != CHOL_OK) return rc;

@@ -1,0 +1,259 @@
+// ozaki.cuh -- binary64-accurate SYRK/GEMM tile updates on the bf16 tensor
+// cores by exact splitting (the Ozaki scheme: Ozaki, Ogita, Oishi, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication", Numer. Algorithms 59, 2012), for tiles of order 128:
+//
+//  * split: every row r of a binary64 tile is scaled by 2^-e_r (e_r = the
+//    exponent of the row's largest magnitude, so the scaled row lies in
+//    (-1, 1)) and cut into S = 8 slices of 7 bits:
+//        x = sum_{s=1..8} a_s 2^{-7 s} + delta,  a_s integer, |a_s| <= 127,
+//    |delta| < 2^-56; every a_s is exact in bf16;
+//  * product: A B^T = 2^{e_r + e_c} sum_d 2^{-7 d} G_d with
+//        G_d = sum_{s + t = d} a_s b_t^T,  d = 2 .. 9  (36 slice products;
+//    the omitted d >= 10 terms are below 2^-53 relative to the row scales).
+//    |sum_k a_s(k) b_t(k)| <= 128 * 127^2 < 2^21 and a group has at most 8
+//    products, so every partial sum of G_d is an integer below 2^24 and the
+//    FP32 accumulation in tensor memory is exact in any order;
+//  * the epilogue combines the 8 groups in binary64 (largest first) and
+//    subtracts the result, scaled back by 2^{e_r + e_c}, from the FP64 tile.
+//
+// The output tile is processed in two halves of 64 columns; a half keeps all
+// 8 group accumulators in tensor memory (8 x 64 = 512 columns) and the 8 B
+// slices of its 64 rows resident in shared memory (128 KB), while the A slices
+// stream through a ring of stages.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "tc_gemm.cuh"
+
+namespace chol {
+
+constexpr int kOzNb = 128;      // tile order of the emulated path
+constexpr int kOzS = 8;         // slices per value
+constexpr int kOzStages = 4;    // A-slice ring
+constexpr int kOzABytes = 128 * 128;  // one A slice, one K-chunk of 64 (bf16): 128 rows x 128 B
+constexpr int kOzBBytes = 64 * 128;   // one B slice, one K-chunk, 64 rows
+
+struct OzShared {
+    uint64_t full[kOzStages];
+    uint64_t empty[kOzStages];
+    uint64_t bfull, bfree, acc_full, tmem_empty, drain;
+    uint32_t tmem_base;
+    uint32_t ring;    // A-stage fills before the current task
+    uint32_t halves;  // halves (B loads / accumulations) before the current task
+    int32_t fail;
+};
+
+struct OzSmem {
+    uint8_t B[2 * kOzS][kOzBBytes];        // 128 KB: slice t, K-chunk kc at index 2 t + kc
+    uint8_t A[kOzStages][kOzABytes];       // 64 KB
+    OzShared os;
+};
+
+__device__ __forceinline__ int oz_failed(const OzShared &s) { return *(volatile const int32_t *)&s.fail; }
+__device__ __forceinline__ void oz_fail(OzShared &s) { *(volatile int32_t *)&s.fail = 1; }
+
+__device__ __forceinline__ double pow2d(int e) {
+    if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(1023 + e) << 52);
+    return ldexp(1.0, e);
+}
+
+// Split a row-major 128 x 128 binary64 tile into 8 bf16 slices ([s][r][c],
+// 32 KB each) and one exponent per row.  All 256 threads; ends with a barrier.
+__device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32_t *rexp) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    for (int r = warp; r < kOzNb; r += 8) {
+        double v[4];
+        double m = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[q] = __ldcg(T + (size_t)r * kOzNb + lane + 32 * q);
+            m = fmax(m, fabs(v[q]));
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        int e = 0;
+        if (m > 0.0 && isfinite(m)) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |row| < 2^e
+        if (lane == 0) rexp[r] = e;
+        const double sc = pow2d(-e);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double x = v[q] * sc;  // exact scaling, |x| < 1
+#pragma unroll
+            for (int s = 0; s < kOzS; ++s) {
+                const double t = x * 128.0;
+                const double a = trunc(t);
+                x = t - a;  // exact
+                slices[(size_t)s * kOzNb * kOzNb + (size_t)r * kOzNb + lane + 32 * q] = __double2bfloat16(a);
+            }
+        }
+    }
+    fence_proxy_async_global();
+    __syncthreads();
+}
+
+inline __device__ void oz_cta_init(OzShared &os) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kOzStages; ++s) {
+            mbar_init(&os.full[s], 1);
+            mbar_init(&os.empty[s], 1);
+        }
+        mbar_init(&os.bfull, 1);
+        mbar_init(&os.bfree, 1);
+        mbar_init(&os.acc_full, 1);
+        mbar_init(&os.tmem_empty, 4);
+        mbar_init(&os.drain, 1);
+        os.ring = 0;
+        os.halves = 0;
+        os.fail = 0;
+        mbar_fence_init();
+    }
+    if (threadIdx.x / 32 == 1) {
+        tmem_alloc(&os.tmem_base, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+inline __device__ void oz_cta_fini(OzShared &os) {
+    __syncthreads();
+    if (threadIdx.x == 32) {
+        tc_commit(&os.drain);
+        mbar_wait(&os.drain, 0, global_ns() + 2000000000ull);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x / 32 == 1) tmem_dealloc(os.tmem_base, 512);
+}
+
+// C (row-major 128 x 128 binary64) -= A B^T where A, B are given by their
+// slices: rows [aRow0, aRow0 + 8*128) and [bRow0, ...) of the slice maps
+// (slice s of a tile at rows base + 128 s) and their row exponents.  mapA has
+// 128-row boxes, mapB 64-row boxes.  Called by all 256 threads; false if a
+// bounded wait expired.
+__device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, const CUtensorMap *mapB, double *C,
+                                         int aRow0, int bRow0, const int32_t *expA, const int32_t *expB,
+                                         uint64_t timeout_ns) {
+    OzShared &os = sm.os;
+    const uint32_t ring0 = os.ring, half0 = os.halves;
+    const uint64_t deadline = global_ns() + timeout_ns;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    constexpr uint32_t kIdesc = make_idesc(OP_BF16, 128, 64);
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        fence_proxy_async_global();
+        uint32_t f = ring0;
+        for (int h = 0; h < 2 && !oz_failed(os); ++h) {
+            const uint32_t u = half0 + h;
+            // the previous half's MMAs must have finished reading the B slices
+            if (u > 0 && !mbar_wait(&os.bfree, (u - 1) & 1, deadline)) {
+                oz_fail(os);
+                break;
+            }
+            mbar_arrive_expect_tx(&os.bfull, 2 * kOzS * kOzBBytes);
+            for (int t = 0; t < kOzS; ++t)
+                for (int kc = 0; kc < 2; ++kc)
+                    tma_load_2d(smem_u32(sm.B[2 * t + kc]), mapB, &os.bfull, kc * 64, bRow0 + t * 128 + h * 64);
+            for (int s = 0; s < kOzS && !oz_failed(os); ++s)
+                for (int kc = 0; kc < 2; ++kc, ++f) {
+                    const int st = (int)(f % kOzStages);
+                    if (f >= (uint32_t)kOzStages &&
+                        !mbar_wait(&os.empty[st], ((f / kOzStages) & 1) ^ 1, deadline)) {
+                        oz_fail(os);
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&os.full[st], kOzABytes);
+                    tma_load_2d(smem_u32(sm.A[st]), mapA, &os.full[st], kc * 64, aRow0 + s * 128);
+                }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        uint32_t f = ring0;
+        for (int h = 0; h < 2 && !oz_failed(os); ++h) {
+            const uint32_t u = half0 + h;
+            if (!mbar_wait(&os.bfull, u & 1, deadline)) {
+                oz_fail(os);
+                break;
+            }
+            if (u > 0 && !mbar_wait(&os.tmem_empty, (u - 1) & 1, deadline)) {
+                oz_fail(os);
+                break;
+            }
+            tc_fence_after();
+            for (int s = 0; s < kOzS && !oz_failed(os); ++s)
+                for (int kc = 0; kc < 2; ++kc, ++f) {
+                    const int st = (int)(f % kOzStages);
+                    if (!mbar_wait(&os.full[st], (f / kOzStages) & 1, deadline)) {
+                        oz_fail(os);
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t abase = smem_u32(sm.A[st]);
+                    for (int t = 0; t + s < kOzS; ++t) {  // group g = s + t (d = g + 2 <= 9)
+                        const uint32_t bbase = smem_u32(sm.B[2 * t + kc]);
+                        const uint32_t d = os.tmem_base + (uint32_t)((s + t) * 64);
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4)
+                            tc_mma<false>(d, sdesc_sw128(abase + k4 * 32), sdesc_sw128(bbase + k4 * 32), kIdesc,
+                                          (s == 0 && kc == 0 && k4 == 0) ? 0u : 1u);
+                    }
+                    tc_commit(&os.empty[st]);
+                }
+            tc_commit(&os.acc_full);
+            tc_commit(&os.bfree);
+        }
+    } else if (warp >= 4) {
+        // ---------------- epilogue: 8 exact FP32 group sums -> binary64
+        const int q = warp - 4;
+        const int row = q * 32 + lane;
+        const double sa = pow2d(__ldcg(expA + row));
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t u = half0 + h;
+            if (!mbar_wait(&os.acc_full, u & 1, deadline)) {
+                oz_fail(os);
+                break;
+            }
+            tc_fence_after();
+            double acc[64];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+#pragma unroll
+            for (int g = 0; g < kOzS; ++g) {
+                const double w = pow2d(-7 * (g + 2));
+#pragma unroll
+                for (int c = 0; c < 64; c += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(os.tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 64 + c), r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[c + j] = fma((double)__uint_as_float(r[j]), w, acc[c + j]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&os.tmem_empty);
+            double *crow = C + (size_t)row * kOzNb + h * 64;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const double sb = pow2d(__ldcg(expB + h * 64 + j));
+                crow[j] = __ldcg(crow + j) - (acc[j] * sa) * sb;
+            }
+        }
+    }
+    __syncthreads();
+    const bool ok = !oz_failed(os);
+    __syncthreads();
+    if (threadIdx.x == 0 && ok) {
+        os.ring = ring0 + 2 * kOzS * 2;
+        os.halves = half0 + 2;
+    }
+    __syncthreads();
+    return ok;
+}
+
+}  // namespace chol

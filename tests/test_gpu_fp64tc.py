@@ -1,0 +1,109 @@
+"""FP64 factorization with SYRK/GEMM on the tensor cores (CHOL_FLAG_FP64_TC):
+binary64 accuracy from exact bf16 slicing.
+
+* the tile update alone: on integer data every slice product is exact, so
+  the update must be exact; on random binary64 data the error must stay at
+  binary64 level, below the bound derived from the splitting:
+  |err| <= 2^-40 * 2^(e_r + e_c) (2^e_r, 2^e_c bound the row and column
+  magnitudes; 56 retained bits, 28 omitted low-order products, 8 rounded
+  binary64 additions);
+* the factorization meets the same FP64 parity bar as the DFMA path
+  (scaled error <= 1e-11 vs the oracle, residual <= 1e-14 sqrt(n)), is exact
+  on Pascal and integer inputs, and the schedules agree bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import seeded_inputs as si
+from gpu_common import TOL_SCALED, gpu_factor, matrix, oracle_factor, probe_residual, resid_bound, scaled_error
+from paper_facts import task_counts
+
+pytestmark = pytest.mark.gpu
+
+
+def _update(A, B, C):
+    import torch
+
+    import paper_2606_11937_gb300 as chol
+    dA = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    dB = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    dC = torch.from_numpy(np.ascontiguousarray(C)).cuda()
+    rc = chol.lib().chol_test_ozaki_update(dA.data_ptr(), dB.data_ptr(), dC.data_ptr())
+    assert rc == 0, chol.chol_last_error()
+    return dC.cpu().numpy()
+
+
+def test_ozaki_update_exact_on_integers():
+    r = si.rng(3)
+    A = r.integers(-1000, 1001, size=(128, 128)).astype(np.float64)
+    B = r.integers(-1000, 1001, size=(128, 128)).astype(np.float64)
+    C = r.integers(-10 ** 6, 10 ** 6, size=(2, 128, 128)).astype(np.float64)
+    got = _update(A, B, C)
+    for k in range(2):
+        assert np.array_equal(got[k], oracle.tile_op("gemm", A, B, C[k]))
+
+
+@pytest.mark.parametrize("scale", ["uniform", "graded"])
+def test_ozaki_update_binary64_accuracy(scale):
+    r = si.rng(4)
+    A = r.standard_normal((128, 128))
+    B = r.standard_normal((128, 128))
+    if scale == "graded":  # rows / columns spanning many binades
+        A *= np.exp2(r.integers(-30, 30, size=(128, 1)))
+        B *= np.exp2(r.integers(-30, 30, size=(128, 1)))
+    C = r.standard_normal((2, 128, 128)) * 10.0
+    got = _update(A, B, C)
+    ea = np.frexp(np.max(np.abs(A), axis=1))[1].astype(np.float64)
+    eb = np.frexp(np.max(np.abs(B), axis=1))[1].astype(np.float64)
+    bound = 2.0 ** -40 * np.exp2(ea[:, None] + eb[None, :])
+    for k in range(2):
+        want = oracle.tile_op("gemm", A, B, C[k])
+        err = np.abs(got[k] - want)
+        tol = bound + 4 * 2.0 ** -53 * np.abs(want)
+        assert np.all(err <= tol), float(np.max(err / tol))
+
+
+@pytest.mark.parametrize("sched", ["dataflow", "fork_join"])
+def test_fp64tc_config1_parity(sched):
+    import paper_2606_11937_gb300 as chol
+    A = matrix("gram", 2048, 0)
+    Lref, _ = oracle_factor("gram", 2048, 0)
+    L, info, st, rc = gpu_factor(A, schedule=sched, flags=chol.CHOL_FLAG_FP64_TC)
+    assert rc == 0 and info == 0 and st.nb == 128
+    assert scaled_error(L, Lref, A) <= TOL_SCALED
+    assert probe_residual(A, L) <= resid_bound(2048)
+    assert tuple(st.tasks) == task_counts(16)
+
+
+def test_fp64tc_ragged_exact_and_schedules():
+    import paper_2606_11937_gb300 as chol
+    f = chol.CHOL_FLAG_FP64_TC
+    P = si.pascal(29)
+    L, info, _, rc = gpu_factor(P, schedule="dataflow", flags=f)
+    assert rc == 0 and np.array_equal(L, si.pascal_lower(29))
+    A, L0 = si.exact_integer_factor(1000, seed=77)
+    outs = []
+    for sched in ("dataflow", "fork_join", "fork_join_naive"):
+        L, info, _, rc = gpu_factor(A, schedule=sched, flags=f)
+        assert rc == 0 and info == 0 and np.array_equal(L, L0)
+    S = matrix("se", 1111, 3, 1e-2)
+    Lref, _ = oracle_factor("se", 1111, 3, 1e-2)
+    for sched in ("dataflow", "fork_join"):
+        L, info, _, rc = gpu_factor(S, schedule=sched, flags=f)
+        assert rc == 0 and info == 0
+        assert scaled_error(L, Lref, S) <= TOL_SCALED
+        outs.append(L)
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_fp64tc_non_spd_info():
+    import paper_2606_11937_gb300 as chol
+    A = matrix("gram", 700, 4).copy()
+    A[301, 301] -= 1000.0
+    _, want = oracle.potrf_unblocked(A)
+    for sched in ("dataflow", "fork_join"):
+        _, info, _, rc = gpu_factor(A, schedule=sched, flags=chol.CHOL_FLAG_FP64_TC)
+        assert rc == 0 and info == want
