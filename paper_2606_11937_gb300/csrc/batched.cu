@@ -281,6 +281,7 @@ int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol
     CHOL_CHECK_ARG(n != nullptr, "n is NULL");
     chol_opts o = resolve_opts(opts);
     CHOL_CHECK_ARG(o.precision == CHOL_FP64 || o.precision == CHOL_FP32, "batched precision must be FP64 or FP32");
+    cudaGetLastError();  // start from a clean error state
     chol_batch_s *p = new chol_batch_s();
     p->batch = batch;
     p->precision = o.precision;
@@ -368,10 +369,12 @@ int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol
             rc = cuda_fail(cudaGetLastError(), "tile list", __FILE__, __LINE__);
             break;
         }
-        // kernel attributes are set before the capture starts
+        // kernel attributes and the occupancy query are settled before the capture starts
         if ((rc = p->precision == CHOL_FP64 ? set_smem_attr<BatchBody<double>>(df_kernel<BatchBody<double>>)
                                             : set_smem_attr<BatchBody<float>>(df_kernel<BatchBody<float>>)) != CHOL_OK)
             break;
+        if (p->precision == CHOL_FP64) df_grid<BatchBody<double>>(0);
+        else df_grid<BatchBody<float>>(0);
         // capture the whole launch sequence once
         if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "capture", __FILE__, __LINE__);

@@ -163,6 +163,7 @@ int chol_factor_ex(int64_t n, double *A, int64_t lda, const chol_opts *opts, int
     CHOL_CHECK_ARG(lda >= (n > 1 ? n : 1), "lda < max(1, n)");
     chol_opts o = resolve_opts(opts);
     CHOL_CHECK_ARG(o.precision == CHOL_FP64, "chol_factor_ex computes in FP64; use chol_mixed_factor");
+    cudaGetLastError();  // errors left by earlier, unrelated runtime calls are not ours to report
     if (stats) memset(stats, 0, sizeof(*stats));
     if (n == 0) return CHOL_OK;
     CHOL_CHECK_ARG(A != nullptr, "A is NULL");

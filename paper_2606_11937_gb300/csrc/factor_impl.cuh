@@ -416,13 +416,22 @@ static __global__ void df_seed_kernel(Control *ctl, DFArgs d, int flags) {
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->tail[q] = (unsigned long long)d.num_matrices;
 }
 
+// Persistent grid size.  The occupancy query runs once per body (never inside
+// a stream capture: batched plans prime it before capturing) and a failed
+// query leaves no error state behind.
 template <class Body>
 int df_grid(int num_ctas) {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, df_kernel<Body>, kThreads, body_smem_bytes<Body>()) !=
-            cudaSuccess ||
-        occ < 1)
-        occ = 1;
+    static int occ_cached = 0;
+    int occ = occ_cached;
+    if (occ == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, df_kernel<Body>, kThreads, body_smem_bytes<Body>()) !=
+                cudaSuccess ||
+            occ < 1) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        occ_cached = occ;
+    }
     const int sms = num_sms();
     const int maxg = sms * occ;
     if (num_ctas <= 0) return sms * (occ < Body::kCtasPerSm ? occ : Body::kCtasPerSm);

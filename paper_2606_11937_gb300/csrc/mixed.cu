@@ -473,6 +473,7 @@ int chol_mixed_factor(int64_t n, const double *A, int64_t lda, const chol_opts *
     CHOL_CHECK_ARG(A != nullptr, "A is NULL");
     chol_opts o = resolve_opts(opts);
     CHOL_CHECK_ARG(o.precision >= CHOL_FP32 && o.precision <= CHOL_FP16, "precision must be FP32, TF32, BF16 or FP16");
+    cudaGetLastError();  // errors left by earlier, unrelated runtime calls are not ours to report
     chol_factor_s *h = new chol_factor_s();
     memset(&g_mixed_stats, 0, sizeof(g_mixed_stats));
     const int rc = mixed_factor_impl(n, A, lda, o, h, info, &g_mixed_stats);

@@ -57,6 +57,7 @@ int chol_solve_ex(int64_t n, int64_t nrhs, const double *L, int64_t ldl, double 
     CHOL_CHECK_ARG(L != nullptr && B != nullptr, "L or B is NULL");
     chol_opts o = resolve_opts(opts);
     cudaStream_t st = (cudaStream_t)o.stream;
+    cudaGetLastError();  // errors left by earlier, unrelated runtime calls are not ours to report
     prepare_pool();
     void *ws = nullptr;
     const size_t bytes = solve_ws_bytes(n, nrhs);

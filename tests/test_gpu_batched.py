@@ -51,6 +51,7 @@ def test_batched_fp64_matches_solo_and_oracle(cap):
             nb = cap if cap > 0 else chol.chol_default_nb(n, "fp64")
             nb = min(nb, n)
             Ls_solo, info_s, _, rc = _solo(A, nb)
+            assert rc == 0, chol.chol_last_error()
             assert np.array_equal(L, Ls_solo), (k, n, nb)
             if n <= 1100:
                 Lref, _ = oracle.potrf_unblocked(A)
