@@ -74,8 +74,8 @@ def test_resident_factor_reuse_and_release():
 
 def test_budget_rejects_oversized_and_admits_the_rest():
     import paper_2606_11937_gb300 as chol
-    srv = chol.Server(64 << 20, slots=2)   # 64 MiB
-    big = si.gram_plus_identity(3000, 1)   # tile store alone exceeds the budget
+    srv = chol.Server(16 << 20, slots=2)   # 16 MiB
+    big = si.gram_plus_identity(3000, 1)   # its FP64 tile store alone (about 37 MB) exceeds the budget
     small = si.gram_plus_identity(200, 2)
     tb, _ = _req(srv, big, si.rhs(3000, 1, seed=1))
     ts, ks = _req(srv, small, si.rhs(200, 1, seed=2))
