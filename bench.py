@@ -232,7 +232,8 @@ def run_fp64(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.n
-    nb = args.nb or chol.chol_default_nb(n, "fp64")
+    tc = bool(args.flags & chol.CHOL_FLAG_FP64_TC)
+    nb = 128 if tc else (args.nb or chol.chol_default_nb(n, "fp64"))
     A0 = si.se_covariance_torch(n, seed=1, lengthscale=0.1, nugget=1e-2, device=dev).T  # column-major view
     A = torch.empty_strided((n, n), (1, n), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)

@@ -247,7 +247,8 @@ int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol
 int chol_batch_run(chol_batch_h plan, double *const *A, const int64_t *lda,
                    double *const *B, int64_t *info);
 
-/* Statistics of the last run: tasks executed (summed) and device time. */
+/* Statistics of the last run: tasks executed (summed) and the device time of
+ * the whole graph (repack, persistent factor+solve kernel, unpack). */
 int chol_batch_stats(chol_batch_h plan, chol_stats *stats);
 
 void chol_batch_free(chol_batch_h plan);
