@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--sweep-nb", default="")
     p.add_argument("--sweep-sched", default="")
     p.add_argument("--noop", action="store_true")
+    p.add_argument("--trace", action="store_true")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--serve-requests", type=int, default=120)
     p.add_argument("--serve-rates", default="20,80,320")

@@ -43,7 +43,8 @@ def run_mixed(args, world, rank, local):
     g.manual_seed(2)
     B = torch.randn((16, n), dtype=torch.float64, device=dev, generator=g).T  # column-major n x 16
     stream = torch.cuda.current_stream(dev)
-    o = chol.opts(precision=prec, schedule=args.schedule, nb=nb, stream=stream.cuda_stream, max_iter=50)
+    o = chol.opts(precision=prec, schedule=args.schedule, nb=nb, stream=stream.cuda_stream, max_iter=50,
+                  flags=args.flags)
     flops = n ** 3 / 3.0
 
     def step():
@@ -88,7 +89,7 @@ def run_mixed(args, world, rank, local):
                        {"workload": f"mixed-precision ({prec} trailing update) tiled Cholesky n={n} nb={nb} "
                                     f"{args.schedule}, SE covariance (l=0.1, nugget 1e-2, seed 1), then solve of 16 "
                                     f"N(0,1) RHS with FP64 refinement to 1e-14",
-                        "n": n, "nb": nb, "precision": prec, "schedule": args.schedule,
+                        "n": n, "nb": nb, "precision": prec, "schedule": args.schedule, "flags": args.flags,
                         "l2": f"inputs larger than L2 ({n * n * 8 / 1e9:.1f} GB FP64 matrix)"},
                        "f32", {"roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                             "frac": achieved / peak, "traffic": None,
@@ -115,10 +116,18 @@ def run_sweep(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     nbs = [int(x) for x in (args.sweep_nb or "64,128,256,512").split(",")]
     scheds = (args.sweep_sched or "dataflow,fork_join,fork_join_naive").split(",")
+    import ctypes
+    import numpy as np
+    rsz = ctypes.sizeof(chol.chol_trace_rec)
     for nb in nbs:
         for sched in scheds:
             for flags in ([0, chol.CHOL_FLAG_NOOP] if args.noop else [0]):
-                o = chol.opts(schedule=sched, nb=nb, flags=flags, stream=stream.cuda_stream)
+                fl = flags | (args.flags & ~chol.CHOL_FLAG_NOOP)
+                m = -(-n // nb)
+                ntask = m * (m + 1) * (m + 2) // 6
+                trace = torch.empty(ntask * rsz, dtype=torch.uint8, device=dev) if args.trace else None
+                o = chol.opts(schedule=sched, nb=nb, flags=fl, stream=stream.cuda_stream, num_ctas=args.num_ctas,
+                              trace=trace, trace_capacity=ntask if args.trace else 0)
                 ts = []
                 for _ in range(max(1, args.steps)):
                     A.copy_(A0)
@@ -128,8 +137,18 @@ def run_sweep(args, world, rank, local):
                 ms = statistics.median(ts)
                 tasks = sum(st.tasks)
                 rec = {"workload": "sweep", "n": n, "nb": nb, "schedule": sched, "noop": bool(flags),
-                       "ms": ms, "tflops": (n ** 3 / 3) / (ms / 1e3) / 1e12 if not flags else None,
+                       "flags": fl, "ms": ms, "tflops": (n ** 3 / 3) / (ms / 1e3) / 1e12 if not flags else None,
                        "tasks": tasks, "us_per_task": 1e3 * ms / tasks, "launches": st.launches}
+                if trace is not None:
+                    raw = trace.cpu().numpy()[: min(st.trace_records, ntask) * rsz]
+                    r = raw.view(np.dtype([("type", "<i4"), ("I", "<i4"), ("K", "<i4"), ("J", "<i4"),
+                                           ("sm", "<i4"), ("matrix", "<i4"), ("t0", "<u8"), ("t1", "<u8")]))
+                    busy_ns = float(np.sum(r["t1"] - r["t0"]))
+                    ctas = args.num_ctas or (152 * 4)
+                    span_ns = float(r["t1"].max() - r["t0"].min())
+                    rec.update({"trace_busy_s": busy_ns / 1e9, "trace_span_s": span_ns / 1e9,
+                                "idle_us_per_task_per_cta": (ctas * span_ns - busy_ns) / 1e3 / len(r),
+                                "mean_task_us": busy_ns / 1e3 / len(r)})
                 if rank == 0:
                     print(json.dumps(rec), flush=True)
 

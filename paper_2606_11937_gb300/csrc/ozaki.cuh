@@ -14,8 +14,9 @@
 //    |sum_k a_s(k) b_t(k)| <= 128 * 127^2 < 2^21 and a group has at most 8
 //    products, so every partial sum of G_d is an integer below 2^24 and the
 //    FP32 accumulation in tensor memory is exact in any order;
-//  * the epilogue combines the 8 groups in binary64 (largest first) and
-//    subtracts the result, scaled back by 2^{e_r + e_c}, from the FP64 tile.
+//  * the epilogue combines the 8 groups exactly into two int64 values and
+//    subtracts them, scaled back by 2^{e_r + e_c}, from the FP64 tile (two
+//    binary64 roundings per element; the FP64 pipe does nothing else).
 //
 // The output tile is processed in two halves of 64 columns; a half keeps all
 // 8 group accumulators in tensor memory (8 x 64 = 512 columns) and the 8 B
@@ -60,10 +61,23 @@ __device__ __forceinline__ double pow2d(int e) {
     return ldexp(1.0, e);
 }
 
+// bf16 bits of a small integer |a| <= 127 with sign `neg` (exact), integer ops only.
+__device__ __forceinline__ uint16_t small_int_bf16(uint32_t a, uint32_t neg) {
+    if (a == 0) return 0;
+    const uint32_t msb = 31u - __clz(a);
+    const uint32_t mant = (a << (7u - msb)) & 0x7Fu;
+    return (uint16_t)((neg << 15) | ((127u + msb) << 7) | mant);
+}
+
 // Split a row-major 128 x 128 binary64 tile into 8 bf16 slices ([s][r][c],
-// 32 KB each) and one exponent per row.  All 256 threads; ends with a barrier.
+// 32 KB each) and one exponent per row.  With x = v 2^-e in (-1, 1) and
+// X = floor(|x| 2^56), slice s (1-based) is sign(x) times bits
+// [56 - 7s, 63 - 7s) of X -- the digits the recursion t = 128 x,
+// a = trunc(t), x = t - a produces -- computed with integer operations on
+// the binary64 encoding.  All 256 threads; ends with a barrier.
 __device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32_t *rexp) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    uint16_t *out = reinterpret_cast<uint16_t *>(slices);
     for (int r = warp; r < kOzNb; r += 8) {
         double v[4];
         double m = 0.0;
@@ -76,21 +90,46 @@ __device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32
         int e = 0;
         if (m > 0.0 && isfinite(m)) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |row| < 2^e
         if (lane == 0) rexp[r] = e;
-        const double sc = pow2d(-e);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            double x = v[q] * sc;  // exact scaling, |x| < 1
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(v[q]);
+            const uint32_t neg = (uint32_t)(bits >> 63);
+            const int expo = (int)((bits >> 52) & 0x7FF);
+            unsigned long long M = bits & ((1ull << 52) - 1);
+            int qexp;                      // |v| = M 2^qexp
+            if (expo == 0) qexp = -1074;   // subnormal or zero
+            else {
+                M |= 1ull << 52;
+                qexp = expo - 1075;
+            }
+            const int sh = qexp - e + 56;  // X = floor(M 2^sh) < 2^56
+            unsigned long long X;
+            if (sh >= 0) X = M << sh;
+            else X = sh <= -64 ? 0ull : (M >> (-sh));
+            uint16_t *o = out + (size_t)r * kOzNb + lane + 32 * q;
 #pragma unroll
             for (int s = 0; s < kOzS; ++s) {
-                const double t = x * 128.0;
-                const double a = trunc(t);
-                x = t - a;  // exact
-                slices[(size_t)s * kOzNb * kOzNb + (size_t)r * kOzNb + lane + 32 * q] = __double2bfloat16(a);
+                const uint32_t a = (uint32_t)((X >> (49 - 7 * s)) & 127u);
+                o[(size_t)s * kOzNb * kOzNb] = small_int_bf16(a, neg);
             }
         }
     }
     fence_proxy_async_global();
     __syncthreads();
+}
+
+// binary64 value of the integer x (|x| < 2^53) times 2^scale, built from the
+// bit pattern with integer operations (exact unless the result leaves the
+// normal range, handled by ldexp).
+__device__ __forceinline__ double int_scaled(long long x, int scale) {
+    if (x == 0) return 0.0;
+    const unsigned long long sign = x < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long ax = x < 0 ? (unsigned long long)(-x) : (unsigned long long)x;
+    const int msb = 63 - __clzll((long long)ax);
+    const int biased = msb + scale + 1023;
+    if (biased < 1 || biased > 2046) return ldexp((double)x, scale);
+    const unsigned long long mant = (ax << (52 - msb)) & ((1ull << 52) - 1);
+    return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | mant));
 }
 
 inline __device__ void oz_cta_init(OzShared &os) {
@@ -209,9 +248,13 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
         }
     } else if (warp >= 4) {
         // ---------------- epilogue: 8 exact FP32 group sums -> binary64
+        // G_g (d = g + 2) are integers below 2^24.  hi = sum_{g<4} G_g 2^{7(3-g)}
+        // and lo = sum_{g>=4} G_g 2^{7(7-g)} are exact int64 (< 2^46); the
+        // update is A B^T = 2^{e_r + e_c} (hi 2^-35 + lo 2^-63), applied as two
+        // binary64 subtractions of exactly scaled values.
         const int q = warp - 4;
         const int row = q * 32 + lane;
-        const double sa = pow2d(__ldcg(expA + row));
+        const int ea = __ldcg(expA + row);
         for (int h = 0; h < 2; ++h) {
             const uint32_t u = half0 + h;
             if (!mbar_wait(&os.acc_full, u & 1, deadline)) {
@@ -219,30 +262,35 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                 break;
             }
             tc_fence_after();
-            double acc[64];
+            double *crow = C + (size_t)row * kOzNb + h * 64;
 #pragma unroll
-            for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+            for (int c = 0; c < 64; c += 32) {
+                long long hi[32], lo[32];
 #pragma unroll
-            for (int g = 0; g < kOzS; ++g) {
-                const double w = pow2d(-7 * (g + 2));
+                for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
 #pragma unroll
-                for (int c = 0; c < 64; c += 32) {
+                for (int g = 0; g < kOzS; ++g) {
                     uint32_t r[32];
                     tmem_ld32(os.tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 64 + c), r);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[c + j] = fma((double)__uint_as_float(r[j]), w, acc[c + j]);
+                    for (int j = 0; j < 32; ++j) {
+                        const long long gv = (long long)__float2int_rn(__uint_as_float(r[j]));
+                        if (g < 4) hi[j] = hi[j] * 128 + gv;
+                        else lo[j] = lo[j] * 128 + gv;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int eab = ea + __ldcg(expB + h * 64 + c + j);
+                    const double dh = int_scaled(hi[j], eab - 35);
+                    const double dl = int_scaled(lo[j], eab - 63);
+                    crow[c + j] = (__ldcg(crow + c + j) - dh) - dl;
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&os.tmem_empty);
-            double *crow = C + (size_t)row * kOzNb + h * 64;
-#pragma unroll
-            for (int j = 0; j < 64; ++j) {
-                const double sb = pow2d(__ldcg(expB + h * 64 + j));
-                crow[j] = __ldcg(crow + j) - (acc[j] * sa) * sb;
-            }
         }
     }
     __syncthreads();
