@@ -146,9 +146,12 @@ def run_sweep(args, world, rank, local):
                     busy_ns = float(np.sum(r["t1"] - r["t0"]))
                     ctas = args.num_ctas or (152 * 4)
                     span_ns = float(r["t1"].max() - r["t0"].min())
-                    rec.update({"trace_busy_s": busy_ns / 1e9, "trace_span_s": span_ns / 1e9,
-                                "idle_us_per_task_per_cta": (ctas * span_ns - busy_ns) / 1e3 / len(r),
-                                "mean_task_us": busy_ns / 1e3 / len(r)})
+                    dur = (r["t1"] - r["t0"]).astype(np.float64)
+                    by_type = {name: float(np.mean(dur[r["type"] == ty]) / 1e3) if np.any(r["type"] == ty) else None
+                               for ty, name in enumerate(("potrf", "trsm", "syrk", "gemm"))}
+                    rec.update({"trace_busy_s": busy_ns / 1e9, "trace_span_s": span_ns / 1e9, "ctas": ctas,
+                                "idle_us_per_task": (ctas * span_ns - busy_ns) / 1e3 / len(r),
+                                "mean_task_us": busy_ns / 1e3 / len(r), "mean_us_by_type": by_type})
                 if rank == 0:
                     print(json.dumps(rec), flush=True)
 
