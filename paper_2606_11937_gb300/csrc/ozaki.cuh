@@ -14,9 +14,10 @@
 //    |sum_k a_s(k) b_t(k)| <= 128 * 127^2 < 2^21 and a group has at most 8
 //    products, so every partial sum of G_d is an integer below 2^24 and the
 //    FP32 accumulation in tensor memory is exact in any order;
-//  * the epilogue combines the 8 groups exactly into two int64 values and
-//    subtracts them, scaled back by 2^{e_r + e_c}, from the FP64 tile (two
-//    binary64 roundings per element; the FP64 pipe does nothing else).
+//  * the epilogue combines the 8 groups exactly into two int64 values, scales
+//    them back by 2^{e_r + e_c} by building the binary64 encodings, adds them
+//    and subtracts the sum from the FP64 tile (two binary64 roundings per
+//    element; the FP64 pipe does nothing else).
 //
 // The output tile is processed in two halves of 64 columns; a half keeps all
 // 8 group accumulators in tensor memory (8 x 64 = 512 columns) and the 8 B
@@ -50,6 +51,8 @@ struct OzShared {
 struct OzSmem {
     uint8_t B[2 * kOzS][kOzBBytes];        // 128 KB: slice t, K-chunk kc at index 2 t + kc
     uint8_t A[kOzStages][kOzABytes];       // 64 KB
+    double xp[4][32 * 32];                 // 32 KB: per epilogue warp, a 32 x 32 transpose buffer
+    int32_t ex[2][kOzNb];                  // row exponents of A and B
     OzShared os;
 };
 
@@ -250,11 +253,19 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
         // ---------------- epilogue: 8 exact FP32 group sums -> binary64
         // G_g (d = g + 2) are integers below 2^24.  hi = sum_{g<4} G_g 2^{7(3-g)}
         // and lo = sum_{g>=4} G_g 2^{7(7-g)} are exact int64 (< 2^46); the
-        // update is A B^T = 2^{e_r + e_c} (hi 2^-35 + lo 2^-63), applied as two
-        // binary64 subtractions of exactly scaled values.
+        // update is A B^T = 2^{e_r + e_c} (hi 2^-35 + lo 2^-63).  Each warp owns
+        // 32 rows; per 32-column chunk its lanes (one row each) form the update
+        // values, pass them through a 32 x 32 shared-memory transpose, and the
+        // warp then subtracts them from C row by row with coalesced accesses.
         const int q = warp - 4;
         const int row = q * 32 + lane;
-        const int ea = __ldcg(expA + row);
+        for (int i = threadIdx.x - 128; i < kOzNb; i += 128) {
+            sm.ex[0][i] = __ldcg(expA + i);
+            sm.ex[1][i] = __ldcg(expB + i);
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");  // the 4 epilogue warps only
+        const int ea = sm.ex[0][row];
+        double *xp = sm.xp[q];
         for (int h = 0; h < 2; ++h) {
             const uint32_t u = half0 + h;
             if (!mbar_wait(&os.acc_full, u & 1, deadline)) {
@@ -262,8 +273,7 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                 break;
             }
             tc_fence_after();
-            double *crow = C + (size_t)row * kOzNb + h * 64;
-#pragma unroll
+#pragma unroll 1
             for (int c = 0; c < 64; c += 32) {
                 long long hi[32], lo[32];
 #pragma unroll
@@ -280,13 +290,23 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                         else lo[j] = lo[j] * 128 + gv;
                     }
                 }
+                // update values of this lane's row, stored transposed: xp[j][lane ^ j]
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int eab = ea + __ldcg(expB + h * 64 + c + j);
+                    const int eab = ea + sm.ex[1][h * 64 + c + j];
                     const double dh = int_scaled(hi[j], eab - 35);
                     const double dl = int_scaled(lo[j], eab - 63);
-                    crow[c + j] = (__ldcg(crow + c + j) - dh) - dl;
+                    xp[j * 32 + (lane ^ j)] = dh + dl;
                 }
+                __syncwarp();
+                // row by row: lane = column
+                double *cbase = C + (size_t)(q * 32) * kOzNb + h * 64 + c + lane;
+#pragma unroll 8
+                for (int rr = 0; rr < 32; ++rr) {
+                    double *p = cbase + (size_t)rr * kOzNb;
+                    *p = __ldcg(p) - xp[lane * 32 + (rr ^ lane)];
+                }
+                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
