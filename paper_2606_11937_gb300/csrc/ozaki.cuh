@@ -135,6 +135,16 @@ __device__ __forceinline__ double int_scaled(long long x, int scale) {
     return __longlong_as_double((long long)(sign | ((unsigned long long)biased << 52) | mant));
 }
 
+// As int_scaled for |x| < 2^47 when the caller knows 1 <= msb + scale + 1023 <= 2046.
+__device__ __forceinline__ double int_scaled_fast(long long x, int scale) {
+    const unsigned long long sign = (unsigned long long)x & (1ull << 63);
+    const unsigned long long ax = (unsigned long long)(x < 0 ? -x : x);
+    const int msb = 63 - __clzll((long long)ax);
+    const unsigned long long mant = (ax << (52 - msb)) & ((1ull << 52) - 1);
+    const unsigned long long bits = sign | ((unsigned long long)(msb + scale + 1023) << 52) | mant;
+    return ax == 0 ? 0.0 : __longlong_as_double((long long)bits);
+}
+
 inline __device__ void oz_cta_init(OzShared &os) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < kOzStages; ++s) {
@@ -227,6 +237,11 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                 break;
             }
             tc_fence_after();
+            // descriptors of the resident B slices; advancing K by 16 bf16 (32 bytes)
+            // adds 2 to the start-address field (16-byte units)
+            uint64_t bdesc[2 * kOzS];
+#pragma unroll
+            for (int i = 0; i < 2 * kOzS; ++i) bdesc[i] = sdesc_sw128(smem_u32(sm.B[i]));
             for (int s = 0; s < kOzS && !oz_failed(os); ++s)
                 for (int kc = 0; kc < 2; ++kc, ++f) {
                     const int st = (int)(f % kOzStages);
@@ -235,13 +250,15 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t abase = smem_u32(sm.A[st]);
-                    for (int t = 0; t + s < kOzS; ++t) {  // group g = s + t (d = g + 2 <= 9)
-                        const uint32_t bbase = smem_u32(sm.B[2 * t + kc]);
+                    const uint64_t adesc = sdesc_sw128(smem_u32(sm.A[st]));
+#pragma unroll
+                    for (int t = 0; t < kOzS; ++t) {  // group g = s + t (d = g + 2 <= 9)
+                        if (t + s >= kOzS) break;
+                        const uint64_t bd = kc ? bdesc[2 * t + 1] : bdesc[2 * t];
                         const uint32_t d = os.tmem_base + (uint32_t)((s + t) * 64);
 #pragma unroll
                         for (int k4 = 0; k4 < 4; ++k4)
-                            tc_mma<false>(d, sdesc_sw128(abase + k4 * 32), sdesc_sw128(bbase + k4 * 32), kIdesc,
+                            tc_mma<false>(d, adesc + 2 * k4, bd + 2 * k4, kIdesc,
                                           (s == 0 && kc == 0 && k4 == 0) ? 0u : 1u);
                     }
                     tc_commit(&os.empty[st]);
@@ -275,28 +292,57 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
             tc_fence_after();
 #pragma unroll 1
             for (int c = 0; c < 64; c += 32) {
+                // group d = g + 2 holds at most d - 1 products below 2^21 each, so
+                // G_{2k} 128 + G_{2k+1} fits in int32; hi = (t01 << 14) + t23 and
+                // lo = (t45 << 14) + t67 are exact int64.
                 long long hi[32], lo[32];
+                const uint32_t tb = os.tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)c;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
+                for (int half4 = 0; half4 < 2; ++half4) {
+                    int32_t t0[32], t1[32];
 #pragma unroll
-                for (int g = 0; g < kOzS; ++g) {
-                    uint32_t r[32];
-                    tmem_ld32(os.tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(g * 64 + c), r);
-                    tmem_ld_wait();
+                    for (int pr = 0; pr < 2; ++pr) {
+                        const int g = half4 * 4 + pr * 2;
+                        uint32_t ra[32], rb[32];
+                        tmem_ld32(tb + (uint32_t)(g * 64), ra);
+                        tmem_ld32(tb + (uint32_t)((g + 1) * 64), rb);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int32_t v = __float2int_rn(__uint_as_float(ra[j])) * 128 +
+                                              __float2int_rn(__uint_as_float(rb[j]));
+                            if (pr == 0) t0[j] = v;
+                            else t1[j] = v;
+                        }
+                    }
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const long long gv = (long long)__float2int_rn(__uint_as_float(r[j]));
-                        if (g < 4) hi[j] = hi[j] * 128 + gv;
-                        else lo[j] = lo[j] * 128 + gv;
+                        const long long w = ((long long)t0[j] << 14) + (long long)t1[j];
+                        if (half4 == 0) hi[j] = w;
+                        else lo[j] = w;
                     }
                 }
                 // update values of this lane's row, stored transposed: xp[j][lane ^ j]
+                // one vote per chunk: exponents of the scaled values stay normal
+                // (|hi|, |lo| < 2^47) unless a row or column scale is extreme
+                bool ok_range = true;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int eab = ea + sm.ex[1][h * 64 + c + j];
-                    const double dh = int_scaled(hi[j], eab - 35);
-                    const double dl = int_scaled(lo[j], eab - 63);
-                    xp[j * 32 + (lane ^ j)] = dh + dl;
+                    ok_range &= (eab >= -900 && eab <= 900);
+                }
+                if (__all_sync(0xffffffffu, ok_range)) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int eab = ea + sm.ex[1][h * 64 + c + j];
+                        xp[j * 32 + (lane ^ j)] = int_scaled_fast(hi[j], eab - 35) + int_scaled_fast(lo[j], eab - 63);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int eab = ea + sm.ex[1][h * 64 + c + j];
+                        xp[j * 32 + (lane ^ j)] = int_scaled(hi[j], eab - 35) + int_scaled(lo[j], eab - 63);
+                    }
                 }
                 __syncwarp();
                 // row by row: lane = column
