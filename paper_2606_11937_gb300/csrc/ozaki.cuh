@@ -276,6 +276,10 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
         // warp then subtracts them from C row by row with coalesced accesses.
         const int q = warp - 4;
         const int row = q * 32 + lane;
+        // pull this row of C into L2 while the MMAs run (8 lines of 128 bytes)
+#pragma unroll
+        for (int l = 0; l < 8; ++l)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (size_t)row * kOzNb + l * 16));
         for (int i = threadIdx.x - 128; i < kOzNb; i += 128) {
             sm.ex[0][i] = __ldcg(expA + i);
             sm.ex[1][i] = __ldcg(expB + i);
@@ -345,13 +349,13 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                     }
                 }
                 __syncwarp();
-                // row by row: lane = column
+                // row by row: lane = column; all 32 row loads in flight first
                 double *cbase = C + (size_t)(q * 32) * kOzNb + h * 64 + c + lane;
-#pragma unroll 8
-                for (int rr = 0; rr < 32; ++rr) {
-                    double *p = cbase + (size_t)rr * kOzNb;
-                    *p = __ldcg(p) - xp[lane * 32 + (rr ^ lane)];
-                }
+                double cv[32];
+#pragma unroll
+                for (int rr = 0; rr < 32; ++rr) cv[rr] = __ldcg(cbase + (size_t)rr * kOzNb);
+#pragma unroll
+                for (int rr = 0; rr < 32; ++rr) cbase[(size_t)rr * kOzNb] = cv[rr] - xp[lane * 32 + (rr ^ lane)];
                 __syncwarp();
             }
             tc_fence_before();
