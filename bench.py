@@ -2,8 +2,10 @@
 
 Default workload (one "step" = one full factorization A = L L^T through the
 C ABI): FP64, n = 32768, squared-exponential covariance of n points uniform in
-the unit square (lengthscale 0.1, nugget 1e-2, seed 1), dataflow schedule.
-Metric: TFLOP/s counting n^3/3 flops per factorization.
+the unit square (lengthscale 0.1, nugget 1e-2, seed 1), dataflow schedule with
+the priority queue, SYRK/GEMM on the tensor cores with binary64 accuracy
+(exact bf16 slicing; --flags 0 selects the DFMA engine).  Metric: TFLOP/s
+counting n^3/3 flops per factorization.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--n 32768] [--nb 256]
                   [--schedule dataflow|fork_join|fork_join_naive]
@@ -63,7 +65,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--flags", type=int, default=0)
+    # default: FP64 SYRK/GEMM on the tensor cores (CHOL_FLAG_FP64_TC = 16) with the
+    # priority ready queue (CHOL_FLAG_PRIORITY = 2); --flags 0 selects the DFMA engine
+    p.add_argument("--flags", type=int, default=-1)
     p.add_argument("--num-ctas", type=int, default=0)
     return p.parse_args()
 
@@ -331,6 +335,8 @@ def run_fp64(args, world, rank, local):
 
 def main():
     args = parse()
+    if args.flags < 0:
+        args.flags = 18 if args.workload == "fp64" else 0
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
