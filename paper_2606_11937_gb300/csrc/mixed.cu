@@ -89,6 +89,7 @@ struct MixedArgs {
 
 struct MixedSmem {
     uint8_t stages[kTcStages][kStageBytes];
+    float xpose[4 * 32 * 32];   // epilogue transpose buffers
     TcShared ts;
 };
 static_assert(sizeof(SimtSmem<double>) <= sizeof(MixedSmem::stages), "SIMT scratch must fit in the stage area");
@@ -215,8 +216,8 @@ struct MixedBody {
                     ga.mapB[p] = (three && p == 1) ? &g.map_lo : &g.map_hi;
                 }
                 ga.idesc = make_idesc((uint32_t)g.fmt, 128, nb >= 256 ? 256 : 128);
-                const bool ok = tc_tile_update(sm.ts, &sm.stages[0][0], ga, g.S.tile(I, K), nb, (int)(ta * nb),
-                                               (int)(tb * nb), sa, sb, type == T_SYRK, g.timeout_ns);
+                const bool ok = tc_tile_update(sm.ts, &sm.stages[0][0], sm.xpose, ga, g.S.tile(I, K), nb,
+                                               (int)(ta * nb), (int)(tb * nb), sa, sb, type == T_SYRK, g.timeout_ns);
                 if (!ok && threadIdx.x == 0) {
                     if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 3;
                     st_release_s32(&a.ctl->abort, 1);
@@ -634,7 +635,7 @@ __global__ void __launch_bounds__(256) tc_test_kernel(const __grid_constant__ Tc
     // two updates in a row exercise the barrier phases across tasks
     bool ok = true;
     for (int rep = 0; rep < 2 && ok; ++rep)
-        ok = tc_tile_update(sm.ts, &sm.stages[0][0], ga, g.C + (size_t)rep * g.nb * g.nb, g.nb, 0, g.nb,
+        ok = tc_tile_update(sm.ts, &sm.stages[0][0], sm.xpose, ga, g.C + (size_t)rep * g.nb * g.nb, g.nb, 0, g.nb,
                             ldexpf(1.f, -g.eA), ldexpf(1.f, -g.eB), g.lower != 0, 2000000000ull);
     if (threadIdx.x == 0) *g.ok = ok ? 1 : 0;
     tc_cta_fini(sm.ts);

@@ -15,9 +15,9 @@
 //    products, so every partial sum of G_d is an integer below 2^24 and the
 //    FP32 accumulation in tensor memory is exact in any order;
 //  * the epilogue combines the 8 groups exactly into two int64 values, scales
-//    them back by 2^{e_r + e_c} by building the binary64 encodings, adds them
-//    and subtracts the sum from the FP64 tile (two binary64 roundings per
-//    element; the FP64 pipe does nothing else).
+//    them back by 2^{e_r + e_c} by building the binary64 encodings, and
+//    subtracts both from the FP64 tile (two binary64 roundings per element; the
+//    FP64 pipe does nothing else).
 //
 // The output tile is processed in two halves of 64 columns; a half keeps all
 // 8 group accumulators in tensor memory (8 x 64 = 512 columns) and the 8 B
@@ -51,7 +51,7 @@ struct OzShared {
 struct OzSmem {
     uint8_t B[2 * kOzS][kOzBBytes];        // 128 KB: slice t, K-chunk kc at index 2 t + kc
     uint8_t A[kOzStages][kOzABytes];       // 64 KB
-    double xp[4][32 * 32];                 // 32 KB: per epilogue warp, a 32 x 32 transpose buffer
+    double xp[4][32 * 32];                 // 32 KB: per epilogue warp, a 32 x 32 block of C
     int32_t ex[2][kOzNb];                  // row exponents of A and B
     OzShared os;
 };
@@ -144,6 +144,16 @@ __device__ __forceinline__ double int_scaled_fast(long long x, int scale) {
     const unsigned long long bits = sign | ((unsigned long long)(msb + scale + 1023) << 52) | mant;
     return ax == 0 ? 0.0 : __longlong_as_double((long long)bits);
 }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+// index of element (r, j) of a warp's 32 x 32 double block in shared memory,
+// 16-byte segments XOR-swizzled by row so row- and column-wise accesses spread
+__device__ __forceinline__ int xp_idx(int r, int j) { return r * 32 + ((((j >> 1) ^ (r & 15)) << 1) | (j & 1)); }
 
 inline __device__ void oz_cta_init(OzShared &os) {
     if (threadIdx.x == 0) {
@@ -271,9 +281,9 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
         // G_g (d = g + 2) are integers below 2^24.  hi = sum_{g<4} G_g 2^{7(3-g)}
         // and lo = sum_{g>=4} G_g 2^{7(7-g)} are exact int64 (< 2^46); the
         // update is A B^T = 2^{e_r + e_c} (hi 2^-35 + lo 2^-63).  Each warp owns
-        // 32 rows; per 32-column chunk its lanes (one row each) form the update
-        // values, pass them through a 32 x 32 shared-memory transpose, and the
-        // warp then subtracts them from C row by row with coalesced accesses.
+        // 32 rows; per 32-column chunk it stages its 32 x 32 block of C in shared
+        // memory with coalesced asynchronous copies, each lane (one row) applies
+        // its row's update there, and the block is written back coalesced.
         const int q = warp - 4;
         const int row = q * 32 + lane;
         // pull this row of C into L2 while the MMAs run (8 lines of 128 bytes)
@@ -296,6 +306,14 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
             tc_fence_after();
 #pragma unroll 1
             for (int c = 0; c < 64; c += 32) {
+                // stage this warp's 32 x 32 block of C in shared memory (async,
+                // coalesced 16-byte copies) while the tensor-memory values are combined
+                double *cblk = C + (size_t)(q * 32) * kOzNb + h * 64 + c;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int idx = i * 32 + lane, rr = idx >> 4, seg = idx & 15;
+                    cp_async16(smem_u32(xp + xp_idx(rr, 2 * seg)), cblk + (size_t)rr * kOzNb + 2 * seg);
+                }
                 // group d = g + 2 holds at most d - 1 products below 2^21 each, so
                 // G_{2k} 128 + G_{2k+1} fits in int32; hi = (t01 << 14) + t23 and
                 // lo = (t45 << 14) + t67 are exact int64.
@@ -326,7 +344,6 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                         else lo[j] = w;
                     }
                 }
-                // update values of this lane's row, stored transposed: xp[j][lane ^ j]
                 // one vote per chunk: exponents of the scaled values stay normal
                 // (|hi|, |lo| < 2^47) unless a row or column scale is extreme
                 bool ok_range = true;
@@ -335,27 +352,31 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                     const int eab = ea + sm.ex[1][h * 64 + c + j];
                     ok_range &= (eab >= -900 && eab <= 900);
                 }
+                cp_async_wait_all();
+                __syncwarp();
+                // this lane's row of the block: C <- (C - hi 2^(eab-35)) - lo 2^(eab-63)
                 if (__all_sync(0xffffffffu, ok_range)) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int eab = ea + sm.ex[1][h * 64 + c + j];
-                        xp[j * 32 + (lane ^ j)] = int_scaled_fast(hi[j], eab - 35) + int_scaled_fast(lo[j], eab - 63);
+                        double &cv = xp[xp_idx(lane, j)];
+                        cv = (cv - int_scaled_fast(hi[j], eab - 35)) - int_scaled_fast(lo[j], eab - 63);
                     }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int eab = ea + sm.ex[1][h * 64 + c + j];
-                        xp[j * 32 + (lane ^ j)] = int_scaled(hi[j], eab - 35) + int_scaled(lo[j], eab - 63);
+                        double &cv = xp[xp_idx(lane, j)];
+                        cv = (cv - int_scaled(hi[j], eab - 35)) - int_scaled(lo[j], eab - 63);
                     }
                 }
                 __syncwarp();
-                // row by row: lane = column; all 32 row loads in flight first
-                double *cbase = C + (size_t)(q * 32) * kOzNb + h * 64 + c + lane;
-                double cv[32];
 #pragma unroll
-                for (int rr = 0; rr < 32; ++rr) cv[rr] = __ldcg(cbase + (size_t)rr * kOzNb);
-#pragma unroll
-                for (int rr = 0; rr < 32; ++rr) cbase[(size_t)rr * kOzNb] = cv[rr] - xp[lane * 32 + (rr ^ lane)];
+                for (int i = 0; i < 16; ++i) {
+                    const int idx = i * 32 + lane, rr = idx >> 4, seg = idx & 15;
+                    const double2 v = *reinterpret_cast<const double2 *>(xp + xp_idx(rr, 2 * seg));
+                    *reinterpret_cast<double2 *>(cblk + (size_t)rr * kOzNb + 2 * seg) = v;
+                }
                 __syncwarp();
             }
             tc_fence_before();

@@ -201,10 +201,12 @@ __device__ __forceinline__ int tc_failed(const TcShared &ts) { return *(volatile
 // C[nb x nb] -= sa * sb * sum_p A_p B_p^T (sa, sb powers of two, applied one
 // after the other so their product never underflows on its own), A rows
 // starting at row aRow0 of the operand maps, B rows at bRow0.  lower: skip
-// sub-tiles strictly above the diagonal (SYRK).  Called by all 256 threads;
+// sub-tiles strictly above the diagonal (SYRK).  xpose: 16 KB of shared memory
+// (four 32 x 32 float transpose buffers).  Called by all 256 threads;
 // returns false if a wait expired.
-__device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, const TcGemmArgs &g, float *C, int nb,
-                                      int aRow0, int bRow0, float sa, float sb, bool lower, uint64_t timeout_ns) {
+__device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpose, const TcGemmArgs &g, float *C,
+                                      int nb, int aRow0, int bRow0, float sa, float sb, bool lower,
+                                      uint64_t timeout_ns) {
     const int MH = nb >= 256 ? 2 : 1;          // 128-row halves per sub-tile
     const int NN = nb >= 256 ? 256 : 128;      // MMA N
     const int SR = MH * 128;                   // sub-tile rows
@@ -284,12 +286,20 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, const TcGem
                 ++u;
             }
     } else if (warp >= 4) {
-        // ---------------- epilogue: TMEM -> registers -> C
+        // ---------------- epilogue: TMEM -> registers -> shared transpose -> C
+        // A lane holds one row of a 32 x 32 chunk; the chunk goes through a
+        // per-warp shared-memory transpose so that C is read and written row by
+        // row with the 32 lanes on 32 consecutive columns (coalesced).
         const int q = warp - 4;  // TMEM lane quadrant of this warp
+        float *xp = xpose + q * 32 * 32;
         uint32_t u = acc0;
         for (int ri = 0; ri < nsr; ++ri)
             for (int ci = 0; ci < nsc; ++ci) {
                 if (skip(ri, ci)) continue;
+                for (int h = 0; h < MH; ++h) {  // pull this warp's rows of the sub-tile into L2
+                    const float *rp = C + (size_t)(ri * SR + h * 128 + q * 32 + lane) * nb + ci * NN;
+                    for (int l = 0; l < NN; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + l));
+                }
                 if (!mbar_wait(&ts.acc_full, u & 1, deadline)) {
                     *(volatile int32_t *)&ts.fail = 1;
                     ri = nsr;
@@ -297,22 +307,21 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, const TcGem
                 }
                 tc_fence_after();
                 for (int h = 0; h < MH; ++h) {
-                    const int row = ri * SR + h * 128 + q * 32 + lane;
-                    float *crow = C + (size_t)row * nb + ci * NN;
+                    const int row0 = ri * SR + h * 128 + q * 32;
                     for (int c = 0; c < NN; c += 32) {
                         uint32_t r[32];
                         tmem_ld32(ts.tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * NN + c), r);
                         tmem_ld_wait();
-                        float4 *cv = reinterpret_cast<float4 *>(crow + c);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            float4 v = __ldcg(cv + j);
-                            v.x -= (__uint_as_float(r[4 * j + 0]) * sa) * sb;
-                            v.y -= (__uint_as_float(r[4 * j + 1]) * sa) * sb;
-                            v.z -= (__uint_as_float(r[4 * j + 2]) * sa) * sb;
-                            v.w -= (__uint_as_float(r[4 * j + 3]) * sa) * sb;
-                            cv[j] = v;
-                        }
+                        for (int j = 0; j < 32; ++j) xp[j * 32 + (lane ^ j)] = (__uint_as_float(r[j]) * sa) * sb;
+                        __syncwarp();
+                        float *cb = C + (size_t)row0 * nb + ci * NN + c + lane;
+                        float cv[32];
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr) cv[rr] = __ldcg(cb + (size_t)rr * nb);
+#pragma unroll
+                        for (int rr = 0; rr < 32; ++rr) cb[(size_t)rr * nb] = cv[rr] - xp[lane * 32 + (rr ^ lane)];
+                        __syncwarp();
                     }
                 }
                 tc_fence_before();
