@@ -49,7 +49,8 @@ struct OzShared {
 };
 
 struct OzSmem {
-    uint8_t B[2 * kOzS][kOzBBytes];        // 128 KB: slice t, K-chunk kc at index 2 t + kc
+    uint8_t B[2 * kOzS][kOzBBytes];        // 128 KB: K-chunk kc, slice t at index kc * 8 + t (so the
+                                           // 8 slices of a K-chunk form one 512-row K-major operand)
     uint8_t A[kOzStages][kOzABytes];       // 64 KB
     double xp[4][32 * 32];                 // 32 KB: per epilogue warp, a 32 x 32 block of C
     int32_t ex[2][kOzNb];                  // row exponents of A and B
@@ -220,7 +221,7 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
             mbar_arrive_expect_tx(&os.bfull, 2 * kOzS * kOzBBytes);
             for (int t = 0; t < kOzS; ++t)
                 for (int kc = 0; kc < 2; ++kc)
-                    tma_load_2d(smem_u32(sm.B[2 * t + kc]), mapB, &os.bfull, kc * 64, bRow0 + t * 128 + h * 64);
+                    tma_load_2d(smem_u32(sm.B[kc * kOzS + t]), mapB, &os.bfull, kc * 64, bRow0 + t * 128 + h * 64);
             for (int s = 0; s < kOzS && !oz_failed(os); ++s)
                 for (int kc = 0; kc < 2; ++kc, ++f) {
                     const int st = (int)(f % kOzStages);
@@ -247,11 +248,16 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                 break;
             }
             tc_fence_after();
-            // descriptors of the resident B slices; advancing K by 16 bf16 (32 bytes)
-            // adds 2 to the start-address field (16-byte units)
-            uint64_t bdesc[2 * kOzS];
-#pragma unroll
-            for (int i = 0; i < 2 * kOzS; ++i) bdesc[i] = sdesc_sw128(smem_u32(sm.B[i]));
+            // For A slice s, the products with B slices t = 0 .. 7-s go to groups
+            // g = s + t, whose accumulators sit at TMEM columns 64 g: contiguous.
+            // With the 8 B slices of a K-chunk stored as one 512-row operand, one
+            // MMA of N = 64 * (number of slices) covers up to 4 of them (N <= 256).
+            // Advancing K by 16 bf16 (32 bytes) adds 2 to the descriptor's
+            // start-address field (16-byte units).
+            const uint64_t bdesc0 = sdesc_sw128(smem_u32(sm.B[0]));
+            const uint64_t bdesc1 = sdesc_sw128(smem_u32(sm.B[kOzS]));
+            constexpr uint32_t kIdescN[5] = {0u, make_idesc(OP_BF16, 128, 64), make_idesc(OP_BF16, 128, 128),
+                                             make_idesc(OP_BF16, 128, 192), make_idesc(OP_BF16, 128, 256)};
             for (int s = 0; s < kOzS && !oz_failed(os); ++s)
                 for (int kc = 0; kc < 2; ++kc, ++f) {
                     const int st = (int)(f % kOzStages);
@@ -261,15 +267,17 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                     }
                     tc_fence_after();
                     const uint64_t adesc = sdesc_sw128(smem_u32(sm.A[st]));
+                    const uint64_t bd = kc ? bdesc1 : bdesc0;
+                    const int nt = kOzS - s;                 // slices t = 0 .. nt-1
+                    const int n1 = nt < 4 ? nt : 4;          // first MMA: t = 0 .. n1-1
+                    const uint32_t d1 = os.tmem_base + (uint32_t)(s * 64);
+                    const uint32_t d2 = os.tmem_base + (uint32_t)((s + 4) * 64);
+                    // B rows of slice 4 start 4 * 64 rows = 32 KB later: +2048 in 16-byte units
 #pragma unroll
-                    for (int t = 0; t < kOzS; ++t) {  // group g = s + t (d = g + 2 <= 9)
-                        if (t + s >= kOzS) break;
-                        const uint64_t bd = kc ? bdesc[2 * t + 1] : bdesc[2 * t];
-                        const uint32_t d = os.tmem_base + (uint32_t)((s + t) * 64);
-#pragma unroll
-                        for (int k4 = 0; k4 < 4; ++k4)
-                            tc_mma<false>(d, adesc + 2 * k4, bd + 2 * k4, kIdesc,
-                                          (s == 0 && kc == 0 && k4 == 0) ? 0u : 1u);
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        const uint32_t acc = (s == 0 && kc == 0 && k4 == 0) ? 0u : 1u;
+                        tc_mma<false>(d1, adesc + 2 * k4, bd + 2 * k4, kIdescN[n1], acc);
+                        if (nt > 4) tc_mma<false>(d2, adesc + 2 * k4, bd + 2048 + 2 * k4, kIdescN[nt - 4], acc);
                     }
                     tc_commit(&os.empty[st]);
                 }
