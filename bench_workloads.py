@@ -57,7 +57,20 @@ def run_mixed(args, world, rank, local):
         st = chol.chol_mixed_last_stats()
         return e0.elapsed_time(e1), st, h
 
-    for _ in range(args.warmup):
+    _, _, h = step()
+    if h.info > 0:
+        # the factorization is not positive definite in this precision: report it
+        if rank == 0:
+            print(json.dumps({"metric": bench.METRIC, "value": None, "unit": "TFLOP/s", "n_gpus": world,
+                              "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                              "config": {"workload": f"mixed-precision ({prec}) tiled Cholesky n={n} nb={nb}",
+                                         "n": n, "nb": nb, "precision": prec},
+                              "status": "breakdown: non-positive pivot in this precision", "info": h.info}),
+                  flush=True)
+        h.close()
+        return
+    h.close()
+    for _ in range(max(0, args.warmup - 1)):
         _, _, h = step()
         h.close()
     torch.cuda.synchronize()

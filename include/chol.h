@@ -211,8 +211,10 @@ int chol_mixed_factor(int64_t n, const double *A, int64_t lda, const chol_opts *
  * is <= opts->refine_tol or after opts->max_iter iterations (options of the
  * factor call).  B: n x nrhs (read only), X: n x nrhs output, both device.
  * iters / berr (host, may be NULL) receive the iterations used and the final
- * backward error.  Returns CHOL_ERR_NOT_CONVERGED if the tolerance was missed
- * (X then holds the best iterate). */
+ * backward error (NaN if an iterate was not finite).  Returns
+ * CHOL_ERR_NOT_CONVERGED if the tolerance was missed (X then holds the last
+ * iterate) and CHOL_ERR_NOT_SPD, without solving, if the handle's
+ * factorization broke down (info > 0). */
 int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb,
                      double *X, int64_t ldx, int32_t *iters, double *berr);
 

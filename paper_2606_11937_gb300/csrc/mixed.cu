@@ -334,6 +334,7 @@ struct chol_factor_s {
     float *store = nullptr;     // binary32 factor tiles
     chol_opts opts{};
     double anorm = -1.0;        // ||A||_inf, computed on first solve
+    int64_t info = 0;           // factorization info (> 0: broke down at that column)
 };
 
 using namespace chol;
@@ -437,6 +438,7 @@ static int mixed_factor_impl(int64_t n, const double *A, int64_t lda, const chol
         cudaFreeAsync(store, st);
     } else {
         *info = hc.info;
+        h->info = hc.info;
         h->n = n;
         h->nb = nb;
         h->M = M;
@@ -514,6 +516,11 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
     }
     const int64_t n = h->n;
     CHOL_CHECK_ARG(nrhs >= 1 && B && X && ldb >= n && ldx >= n, "bad B / X arguments");
+    if (h->info > 0) {
+        set_error("the factorization broke down at column %lld (not positive definite in this precision)",
+                  (long long)h->info);
+        return CHOL_ERR_NOT_SPD;
+    }
     const chol_opts &o = h->opts;
     cudaStream_t st = (cudaStream_t)o.stream;
     prepare_pool();
@@ -562,6 +569,7 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
                 break;
             }
             berr = 0.0;
+            bool finite = true;
             for (int64_t c = 0; c < nrhs; ++c) {
                 double r, x, b;
                 memcpy(&r, &hm[3 * c], 8);
@@ -569,8 +577,10 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
                 memcpy(&b, &hm[3 * c + 2], 8);
                 const double den = h->anorm * x + b;
                 const double e = den > 0 ? r / den : r;
-                berr = e > berr ? e : berr;
+                if (!(e <= 1e300)) finite = false;  // NaN or Inf: the iterate is unusable
+                else berr = e > berr ? e : berr;
             }
+            if (!finite) berr = __builtin_nan("");
             if (berr <= o.refine_tol || it >= o.max_iter || !(berr == berr)) break;
             // d = L^-T L^-1 r in binary32 on the tile store; x += d
             to_f32_kernel<<<vgrid, 256, 0, st>>>(R, n, D, n, nrhs);

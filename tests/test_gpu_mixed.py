@@ -127,3 +127,17 @@ def test_mixed_non_spd_info():
             rc, h, dA = mixed(A, prec, sched, 128)
             assert rc == 0 and h.info == want
             h.close()
+
+
+def test_breakdown_is_reported_not_solved():
+    """A factor that broke down (info > 0) refuses to solve; NaN never
+    passes as converged."""
+    import paper_2606_11937_gb300 as chol
+    n = 1024
+    A = matrix("gram", n, 4).copy()
+    A[500, 500] = -1.0
+    rc, h, dA = mixed(A, "bf16", "dataflow", 128)
+    assert rc == 0 and h.info > 0
+    rc, X, iters, berr = h.solve(chol.colmajor(si.rhs(n, 2, seed=1)), raise_on_error=False)
+    assert rc == chol.CHOL_ERR_NOT_SPD
+    h.close()
