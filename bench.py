@@ -62,6 +62,9 @@ def parse():
     p.add_argument("--serve-slots", type=int, default=4)
     p.add_argument("--serve-budget-gb", type=float, default=64.0)
     p.add_argument("--precision", default="fp32")
+    p.add_argument("--nugget", type=float, default=1e-2, help="SE covariance nugget (mixed workload)")
+    p.add_argument("--no-fp64-compare", action="store_true",
+                   help="mixed workload: skip the FP64 factor+solve time-to-solution comparison")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")

@@ -3,10 +3,13 @@
 Each prints one JSON line with the keys of the default FP64 line.
 
 * mixed: mixed-precision factorization (trailing SYRK/GEMM on tcgen05) of
-  the SE covariance (n, nugget 1e-2), then a solve of 16 N(0, 1) right-hand
-  sides with FP64 iterative refinement to backward error 1e-14.  value =
-  factorization TFLOP/s (n^3/3); the line also carries the refinement
-  iterations, the backward error and the time to solution.
+  the SE covariance (n, --nugget, default 1e-2), then a solve of 16 N(0, 1)
+  right-hand sides with FP64 iterative refinement to backward error 1e-14.
+  value = factorization TFLOP/s (n^3/3); the line also carries the
+  refinement iterations, the backward error, the time to solution and the
+  plain FP64 path's time to solution (factor + solve) on the same inputs.
+  A factorization that breaks down (not positive definite in the chosen
+  precision) prints its info instead of a value.
 * sweep: FP64 factorization time for every tile order x schedule (the
   paper's tile-size sweep, Section 4.1, on the GPU); one line per point.
 """
@@ -38,7 +41,7 @@ def run_mixed(args, world, rank, local):
     n = args.n
     prec = args.precision
     nb = args.nb or chol.chol_default_nb(n, prec)
-    A = si.se_covariance_torch(n, seed=1, lengthscale=0.1, nugget=1e-2, device=dev).T
+    A = si.se_covariance_torch(n, seed=1, lengthscale=0.1, nugget=args.nugget, device=dev).T
     g = torch.Generator(device=dev)
     g.manual_seed(2)
     B = torch.randn((16, n), dtype=torch.float64, device=dev, generator=g).T  # column-major n x 16
@@ -63,8 +66,9 @@ def run_mixed(args, world, rank, local):
         if rank == 0:
             print(json.dumps({"metric": bench.METRIC, "value": None, "unit": "TFLOP/s", "n_gpus": world,
                               "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                              "config": {"workload": f"mixed-precision ({prec}) tiled Cholesky n={n} nb={nb}",
-                                         "n": n, "nb": nb, "precision": prec},
+                              "config": {"workload": f"mixed-precision ({prec}) tiled Cholesky n={n} nb={nb}, "
+                                                     f"SE covariance (l=0.1, nugget {args.nugget:g}, seed 1)",
+                                         "n": n, "nb": nb, "precision": prec, "nugget": args.nugget},
                               "status": "breakdown: non-positive pivot in this precision", "info": h.info}),
                   flush=True)
         h.close()
@@ -91,6 +95,7 @@ def run_mixed(args, world, rank, local):
     torch.cuda.synchronize()
     solve_s = time.perf_counter() - t
     h.close()
+    fp64 = None if args.no_fp64_compare else _fp64_time_to_solution(A, B, stream, chol)
     ms = bench.allreduce_max(statistics.mean(times), world)
     value = world * flops / (ms / 1e3) / 1e12
     achieved = flops / (statistics.mean(kms) / 1e3) / 1e12
@@ -100,9 +105,10 @@ def run_mixed(args, world, rank, local):
     if rank == 0:
         line = _common(args, world, value, "TFLOP/s", ms,
                        {"workload": f"mixed-precision ({prec} trailing update) tiled Cholesky n={n} nb={nb} "
-                                    f"{args.schedule}, SE covariance (l=0.1, nugget 1e-2, seed 1), then solve of 16 "
-                                    f"N(0,1) RHS with FP64 refinement to 1e-14",
+                                    f"{args.schedule}, SE covariance (l=0.1, nugget {args.nugget:g}, seed 1), then solve "
+                                    f"of 16 N(0,1) RHS with FP64 refinement to 1e-14",
                         "n": n, "nb": nb, "precision": prec, "schedule": args.schedule, "flags": args.flags,
+                        "nugget": args.nugget,
                         "l2": f"inputs larger than L2 ({n * n * 8 / 1e9:.1f} GB FP64 matrix)"},
                        "f32", {"roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                             "frac": achieved / peak, "traffic": None,
@@ -110,8 +116,50 @@ def run_mixed(args, world, rank, local):
                                             "peak_source": f"measured bf16 {bf16} TFLOP/s x nominal ratio for {prec}"},
                                "refinement": {"status": rc, "iterations": iters, "berr": berr,
                                               "solve_s": solve_s, "time_to_solution_s": ms / 1e3 + solve_s},
+                               "fp64_reference_path": fp64,
                                "clocks": clk.summary()})
         print(json.dumps(line), flush=True)
+
+
+def _berr(A, X, B):
+    """max over columns of ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)."""
+    import torch
+    R = B - A @ X
+    an = torch.max(torch.sum(torch.abs(A), dim=1))
+    num = torch.max(torch.abs(R), dim=0).values
+    den = an * torch.max(torch.abs(X), dim=0).values + torch.max(torch.abs(B), dim=0).values
+    return float(torch.max(num / den))
+
+
+def _fp64_time_to_solution(A, B, stream, chol):
+    """The plain FP64 path on the same inputs: chol_factor_ex (tensor-core
+    engine, exact slicing) + chol_solve_ex, device time, with its backward
+    error; the second of two runs is reported."""
+    import torch
+    n = A.shape[0]
+    o = chol.opts(schedule="dataflow", nb=128, flags=chol.CHOL_FLAG_FP64_TC | chol.CHOL_FLAG_PRIORITY,
+                  stream=stream.cuda_stream)
+    L = torch.empty_strided((n, n), (1, n), dtype=torch.float64, device=A.device)
+    out = None
+    for _ in range(2):
+        L.copy_(A)
+        X = B.clone()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, info, _ = chol.chol_factor_ex(L, o)
+        e1.record(stream)
+        chol.chol_solve_ex(L, X, o)
+        e2.record(stream)
+        e2.synchronize()
+        out = {"engine": "fp64 tensor-core (exact slicing), dataflow nb=128", "info": info,
+               "factor_s": e0.elapsed_time(e1) / 1e3, "solve_s": e1.elapsed_time(e2) / 1e3,
+               "time_to_solution_s": e0.elapsed_time(e2) / 1e3}
+    out["berr"] = _berr(A, X, B)
+    del L
+    return out
 
 
 def run_sweep(args, world, rank, local):
