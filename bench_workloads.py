@@ -205,7 +205,7 @@ def run_sweep(args, world, rank, local):
                     r = raw.view(np.dtype([("type", "<i4"), ("I", "<i4"), ("K", "<i4"), ("J", "<i4"),
                                            ("sm", "<i4"), ("matrix", "<i4"), ("t0", "<u8"), ("t1", "<u8")]))
                     busy_ns = float(np.sum(r["t1"] - r["t0"]))
-                    ctas = args.num_ctas or (152 * 4)
+                    ctas = args.num_ctas or 152 * (1 if fl & chol.CHOL_FLAG_FP64_TC else 4)
                     span_ns = float(r["t1"].max() - r["t0"].min())
                     dur = (r["t1"] - r["t0"]).astype(np.float64)
                     by_type = {name: float(np.mean(dur[r["type"] == ty]) / 1e3) if np.any(r["type"] == ty) else None

@@ -299,41 +299,81 @@ __device__ __forceinline__ void df_push(Control *ctl, const DFArgs &d, int q, ui
 
 // Pop one task (thread 0).  Returns 1 (task in *out), 0 (all tasks done) or
 // -1 (abort, failure elsewhere, or a wait longer than the timeout).
-static __device__ int df_pop(Control *ctl, const DFArgs &d, uint64_t *out) {
+//
+// The priority queue is popped by compare-and-swap on its head (few tasks,
+// short bursts).  The normal queue is popped by ticket: a CTA takes the next
+// slot index with one fetch-and-add and keeps it (*ticket) until a push fills
+// that slot, checking the priority queue meanwhile; there is no retry storm on
+// a contended head.  Slots are handed out in push order, so the queue stays
+// FIFO; a ticket past the last normal task is never filled and is dropped
+// when every task has completed.
+constexpr unsigned long long kNoTicket = ~0ull;
+constexpr int kLookahead = 4;  // panel columns ahead whose updates are prioritized
+
+static __device__ int df_pop(Control *ctl, const DFArgs &d, uint64_t *out, unsigned long long *ticket) {
     const uint64_t t0 = global_ns();
-    uint32_t backoff = 64;
+    uint32_t backoff = 32;
     for (;;) {
-        if (ld_acquire_s32(&ctl->abort)) return -1;
-        if (ld_relaxed_u64(&ctl->completed) >= (uint64_t)d.total) return 0;
-        bool retry = false;
-        for (int q = 0; q < 2 && !retry; ++q) {
-            const unsigned long long h = ld_relaxed_u64(&ctl->head[q]);
-            const unsigned long long t = ld_acquire_u64(&ctl->tail[q]);
-            if (h < t) {
-                if (atomicCAS(&ctl->head[q], h, h + 1) == h) {
-                    const unsigned long long *slot = &d.queue[(size_t)q * d.capacity + h];
-                    uint64_t v;
-                    // the pusher reserved this slot before we saw it: it is written shortly
-                    while ((v = ld_acquire_u64(slot)) == kEmptySlot) {
-                        if (global_ns() - t0 > d.timeout_ns) {
-                            df_timeout(ctl, 2);
-                            return -1;
-                        }
+        // independent loads, issued together (one round trip to L2)
+        const int32_t ab = ld_acquire_s32(&ctl->abort);
+        const unsigned long long done = ld_relaxed_u64(&ctl->completed);
+        const unsigned long long h = ld_relaxed_u64(&ctl->head[0]);
+        const unsigned long long t = ld_acquire_u64(&ctl->tail[0]);
+        const bool have = *ticket < (unsigned long long)d.capacity;
+        const uint64_t v = have ? ld_acquire_u64(&d.queue[(size_t)d.capacity + *ticket]) : kEmptySlot;
+        if (ab) return -1;
+        if (done >= (uint64_t)d.total) return 0;
+        if (h < t) {
+            if (atomicCAS(&ctl->head[0], h, h + 1) == h) {
+                const unsigned long long *slot = &d.queue[h];
+                uint64_t w;
+                // the pusher reserved this slot before we saw it: it is written shortly
+                while ((w = ld_acquire_u64(slot)) == kEmptySlot) {
+                    if (global_ns() - t0 > d.timeout_ns) {
+                        df_timeout(ctl, 2);
+                        return -1;
                     }
-                    *out = v;
-                    return 1;
                 }
-                retry = true;  // lost the race for this slot: look again at once
+                *out = w;
+                return 1;
             }
+            continue;  // lost the race for this slot: look again at once
         }
-        if (retry) continue;
+        if (v != kEmptySlot) {
+            *ticket = kNoTicket;
+            *out = v;
+            return 1;
+        }
+        if (*ticket == kNoTicket) {
+            *ticket = atomicAdd(&ctl->head[1], 1ull);
+            continue;
+        }
         if (global_ns() - t0 > d.timeout_ns) {
             df_timeout(ctl, 1);
             return -1;
         }
         nanosleep_ns(backoff);
-        backoff = backoff < 2048 ? backoff * 2 : 2048;
+        backoff = backoff < 512 ? backoff * 2 : 512;
     }
+}
+
+// Priority class (with CHOL_FLAG_PRIORITY): the tasks that lead to the next
+// POTRFs -- POTRF, TRSM, SYRK and the GEMMs that update one of the next
+// kLookahead panel columns (K <= J + kLookahead).
+__device__ __forceinline__ bool df_is_priority(int flags, int I, int K, int J) {
+    return (flags & CHOL_FLAG_PRIORITY) && (task_type(I, K, J) != T_GEMM || K <= J + kLookahead);
+}
+
+// Count one finished predecessor of the tile-chain successor (I, K, J) and
+// return its packed word if that made it ready (the caller runs it next, on
+// the same CTA, without a trip through the queue), else kEmptySlot.
+template <class Body>
+__device__ __forceinline__ uint64_t df_release_chain(const typename Body::Args &g, const SchedArgs &a,
+                                                     const DFArgs &d, int m, int M, int I, int K, int J) {
+    if ((a.flags & CHOL_FLAG_TEST_WITHHOLD) && I == M - 1 && K == M - 1 && J == M - 1) return kEmptySlot;
+    const int64_t id = Body::task_base(g, m) + task_id(I, K, J);
+    const int32_t old = atom_add_acqrel_s32(&d.deps[id], 1);
+    return old + 1 == task_needs(I, K, J) ? pack_task(m, I, K, J) : kEmptySlot;
 }
 
 template <class Body>
@@ -343,20 +383,18 @@ __device__ __forceinline__ void df_notify_one(const typename Body::Args &g, cons
     const int32_t need = task_needs(I, K, J);
     const int64_t id = Body::task_base(g, m) + task_id(I, K, J);
     const int32_t old = atom_add_acqrel_s32(&d.deps[id], 1);
-    if (old + 1 == need) {
-        const int type = task_type(I, K, J);
-        const int q = ((a.flags & CHOL_FLAG_PRIORITY) && type != T_GEMM) ? 0 : 1;
-        df_push(a.ctl, d, q, pack_task(m, I, K, J));
-    }
+    if (old + 1 == need) df_push(a.ctl, d, df_is_priority(a.flags, I, K, J) ? 0 : 1, pack_task(m, I, K, J));
 }
 
 // Successors of task (I, K, J) of matrix m, released by the 32 lanes of warp 0.
+// The successor of an update on its tile's chain is not queued when it
+// becomes ready: lane 0 gets it in *cont and the CTA runs it next.
 template <class Body>
 __device__ void df_notify(const typename Body::Args &g, const SchedArgs &a, const DFArgs &d, int m, int I, int K,
-                          int J, int lane) {
+                          int J, int lane, uint64_t *cont) {
     const int M = Body::tiles(g, m);
     if (J < K) {                       // an update: the next task of the tile's chain
-        if (lane == 0) df_notify_one<Body>(g, a, d, m, M, I, K, J + 1);
+        if (lane == 0) *cont = df_release_chain<Body>(g, a, d, m, M, I, K, J + 1);
     } else if (I == K) {               // POTRF(K): every TRSM(I2, K)
         for (int I2 = K + 1 + lane; I2 < M; I2 += 32) df_notify_one<Body>(g, a, d, m, M, I2, K, K);
         if (Body::kSolveTask && K == M - 1 && lane == 0) df_push(a.ctl, d, 0, pack_task(m, M, M, kSolveJ));
@@ -377,10 +415,33 @@ __global__ void __launch_bounds__(256) df_kernel(const __grid_constant__ typenam
     __shared__ int s_cmd;
     Control *ctl = a.ctl;
     Body::cta_init(g, sm);
+    unsigned long long ticket = kNoTicket;  // thread 0: claimed slot of the normal queue
+    uint64_t cont = kEmptySlot;             // thread 0: ready chain successor of the last task
     for (;;) {
         if (threadIdx.x == 0) {
             uint64_t v = 0;
-            const int cmd = df_pop(ctl, d, &v);
+            int cmd = 0;
+            if (cont != kEmptySlot) {
+                // run the chain successor here, unless it is a normal-class task
+                // and priority work is waiting: then it goes to the normal queue
+                const int cj = (int)(cont & 0xffff), ck = (int)((cont >> 16) & 0xffff);
+                const int ci = (int)((cont >> 32) & 0xffff);
+                bool run_here = true;
+                if ((a.flags & CHOL_FLAG_PRIORITY) && !df_is_priority(a.flags, ci, ck, cj)) {
+                    const unsigned long long h = ld_relaxed_u64(&ctl->head[0]);
+                    const unsigned long long t = ld_acquire_u64(&ctl->tail[0]);
+                    if (h < t) {
+                        df_push(ctl, d, 1, cont);
+                        run_here = false;
+                    }
+                }
+                if (run_here) {
+                    cmd = ld_acquire_s32(&ctl->abort) ? -1 : 1;
+                    v = cont;
+                }
+                cont = kEmptySlot;
+            }
+            if (cmd == 0) cmd = df_pop(ctl, d, &v, &ticket);
             if (cmd == 1) fence_acq_rel();
             s_task = v;
             s_cmd = cmd;
@@ -400,7 +461,8 @@ __global__ void __launch_bounds__(256) df_kernel(const __grid_constant__ typenam
         if (threadIdx.x < 32) {
             fence_acq_rel();                   // publish this CTA's tile writes (cumulative after the barrier)
             __syncwarp();
-            if (J != kSolveJ && !ld_relaxed_s32(&ctl->abort)) df_notify<Body>(g, a, d, m, I, K, J, threadIdx.x);
+            if (J != kSolveJ && !ld_relaxed_s32(&ctl->abort))
+                df_notify<Body>(g, a, d, m, I, K, J, threadIdx.x, &cont);
             __syncwarp();
             if (threadIdx.x == 0) atomicAdd(&ctl->completed, 1ull);
         }

@@ -20,7 +20,7 @@ static int make_slice_map(CUtensorMap *map, void *base, int64_t rows, int box_ro
 
 struct OzArgs {
     CUtensorMap mapA;   // slice store, 128-row boxes
-    CUtensorMap mapB;   // slice store, 64-row boxes
+    CUtensorMap mapB;   // slice store, 32-row boxes (one quarter of a tile)
     TileStore<double> S;
     __nv_bfloat16 *slices;  // per tile: 8 slices of 128 x 128
     int32_t *rexp;          // per tile: 128 row exponents
@@ -100,7 +100,7 @@ int fp64tc_schedule(double *store, int64_t n, Control *ctl, unsigned long long *
     g.rexp = (int32_t *)((char *)ws + b_sl);
     g.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
     int rc = make_slice_map(&g.mapA, g.slices, tiles * kOzS * kOzNb, 128);
-    if (rc == CHOL_OK) rc = make_slice_map(&g.mapB, g.slices, tiles * kOzS * kOzNb, 64);
+    if (rc == CHOL_OK) rc = make_slice_map(&g.mapB, g.slices, tiles * kOzS * kOzNb, kOzQ);
     SchedArgs a{ctl, o.trace, o.trace_capacity, o.flags, 0};
     if (rc == CHOL_OK) {
         if (sched == CHOL_SCHED_DATAFLOW) {
@@ -168,7 +168,7 @@ int chol_test_ozaki_update(const double *A, const double *B, double *C) {
     OzTestArgs g;
     memset(&g, 0, sizeof(g));
     int rc = make_slice_map(&g.mapA, sl, 2 * kOzS * kOzNb, 128);
-    if (rc == CHOL_OK) rc = make_slice_map(&g.mapB, sl, 2 * kOzS * kOzNb, 64);
+    if (rc == CHOL_OK) rc = make_slice_map(&g.mapB, sl, 2 * kOzS * kOzNb, kOzQ);
     if (rc == CHOL_OK) {
         g.C = C;
         g.rexp = rexp;

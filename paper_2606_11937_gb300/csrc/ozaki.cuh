@@ -19,10 +19,12 @@
 //    subtracts both from the FP64 tile (two binary64 roundings per element; the
 //    FP64 pipe does nothing else).
 //
-// The output tile is processed in two halves of 64 columns; a half keeps all
-// 8 group accumulators in tensor memory (8 x 64 = 512 columns) and the 8 B
-// slices of its 64 rows resident in shared memory (128 KB), while the A slices
-// stream through a ring of stages.
+// The output tile is processed in four quarters of 32 columns.  A quarter's 8
+// group accumulators take 8 x 32 = 256 tensor-memory columns, so two quarters
+// alternate between the two halves of the 512 columns: the epilogue of one
+// quarter runs while the tensor cores accumulate the next.  The 8 B slices of
+// a quarter's 32 rows (64 KB) are double-buffered in shared memory as well;
+// the A slices stream through a ring of stages.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -35,22 +37,23 @@ namespace chol {
 constexpr int kOzNb = 128;      // tile order of the emulated path
 constexpr int kOzS = 8;         // slices per value
 constexpr int kOzStages = 4;    // A-slice ring
+constexpr int kOzQ = 32;        // output columns per quarter (B rows per slice and quarter)
 constexpr int kOzABytes = 128 * 128;  // one A slice, one K-chunk of 64 (bf16): 128 rows x 128 B
-constexpr int kOzBBytes = 64 * 128;   // one B slice, one K-chunk, 64 rows
+constexpr int kOzBBytes = kOzQ * 128; // one B slice, one K-chunk, one quarter's 32 rows
 
 struct OzShared {
     uint64_t full[kOzStages];
     uint64_t empty[kOzStages];
-    uint64_t bfull, bfree, acc_full, tmem_empty, drain;
+    uint64_t bfull[2], bfree[2], acc_full[2], tmem_empty[2], drain;
     uint32_t tmem_base;
-    uint32_t ring;    // A-stage fills before the current task
-    uint32_t halves;  // halves (B loads / accumulations) before the current task
+    uint32_t ring;      // A-stage fills before the current task
+    uint32_t quarters;  // quarters (B loads / accumulations) before the current task
     int32_t fail;
 };
 
 struct OzSmem {
-    uint8_t B[2 * kOzS][kOzBBytes];        // 128 KB: K-chunk kc, slice t at index kc * 8 + t (so the
-                                           // 8 slices of a K-chunk form one 512-row K-major operand)
+    uint8_t B[2][2 * kOzS][kOzBBytes];     // 128 KB: buffer b, K-chunk kc, slice t at [b][kc * 8 + t] (the
+                                           // 8 slices of a K-chunk form one 256-row K-major operand)
     uint8_t A[kOzStages][kOzABytes];       // 64 KB
     double xp[4][32 * 32];                 // 32 KB: per epilogue warp, a 32 x 32 block of C
     int32_t ex[2][kOzNb];                  // row exponents of A and B
@@ -162,13 +165,15 @@ inline __device__ void oz_cta_init(OzShared &os) {
             mbar_init(&os.full[s], 1);
             mbar_init(&os.empty[s], 1);
         }
-        mbar_init(&os.bfull, 1);
-        mbar_init(&os.bfree, 1);
-        mbar_init(&os.acc_full, 1);
-        mbar_init(&os.tmem_empty, 4);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&os.bfull[b], 1);
+            mbar_init(&os.bfree[b], 1);
+            mbar_init(&os.acc_full[b], 1);
+            mbar_init(&os.tmem_empty[b], 4);
+        }
         mbar_init(&os.drain, 1);
         os.ring = 0;
-        os.halves = 0;
+        os.quarters = 0;
         os.fail = 0;
         mbar_fence_init();
     }
@@ -196,32 +201,36 @@ inline __device__ void oz_cta_fini(OzShared &os) {
 // C (row-major 128 x 128 binary64) -= A B^T where A, B are given by their
 // slices: rows [aRow0, aRow0 + 8*128) and [bRow0, ...) of the slice maps
 // (slice s of a tile at rows base + 128 s) and their row exponents.  mapA has
-// 128-row boxes, mapB 64-row boxes.  Called by all 256 threads; false if a
+// 128-row boxes, mapB 32-row boxes.  Called by all 256 threads; false if a
 // bounded wait expired.
+//
+// Quarter u (counted across tasks) uses B buffer and tensor-memory half
+// b = u & 1; the k-th use of a buffer waits on its barriers with parity k & 1.
 __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, const CUtensorMap *mapB, double *C,
                                          int aRow0, int bRow0, const int32_t *expA, const int32_t *expB,
                                          uint64_t timeout_ns) {
     OzShared &os = sm.os;
-    const uint32_t ring0 = os.ring, half0 = os.halves;
+    const uint32_t ring0 = os.ring, q0 = os.quarters;
     const uint64_t deadline = global_ns() + timeout_ns;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    constexpr uint32_t kIdesc = make_idesc(OP_BF16, 128, 64);
+    constexpr int kQuarters = kOzNb / kOzQ;
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
         fence_proxy_async_global();
         uint32_t f = ring0;
-        for (int h = 0; h < 2 && !oz_failed(os); ++h) {
-            const uint32_t u = half0 + h;
-            // the previous half's MMAs must have finished reading the B slices
-            if (u > 0 && !mbar_wait(&os.bfree, (u - 1) & 1, deadline)) {
+        for (int qq = 0; qq < kQuarters && !oz_failed(os); ++qq) {
+            const uint32_t u = q0 + qq, b = u & 1;
+            // the MMAs of quarter u - 2 must have finished reading buffer b
+            if (u >= 2 && !mbar_wait(&os.bfree[b], ((u >> 1) - 1) & 1, deadline)) {
                 oz_fail(os);
                 break;
             }
-            mbar_arrive_expect_tx(&os.bfull, 2 * kOzS * kOzBBytes);
+            mbar_arrive_expect_tx(&os.bfull[b], 2 * kOzS * kOzBBytes);
             for (int t = 0; t < kOzS; ++t)
                 for (int kc = 0; kc < 2; ++kc)
-                    tma_load_2d(smem_u32(sm.B[kc * kOzS + t]), mapB, &os.bfull, kc * 64, bRow0 + t * 128 + h * 64);
+                    tma_load_2d(smem_u32(sm.B[b][kc * kOzS + t]), mapB, &os.bfull[b], kc * 64,
+                                bRow0 + t * 128 + qq * kOzQ);
             for (int s = 0; s < kOzS && !oz_failed(os); ++s)
                 for (int kc = 0; kc < 2; ++kc, ++f) {
                     const int st = (int)(f % kOzStages);
@@ -236,28 +245,31 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
+        // For A slice s, the products with B slices t = 0 .. 7-s go to groups
+        // g = s + t, whose accumulators sit at tensor-memory columns 32 g of the
+        // quarter's half: contiguous, so with the 8 B slices of a K-chunk stored
+        // as one 256-row operand a single MMA of N = 32 (8 - s) covers them all.
+        // Advancing K by 16 bf16 (32 bytes) adds 2 to the descriptor's
+        // start-address field (16-byte units).
+        constexpr uint32_t kIdescN[kOzS + 1] = {
+            0u, make_idesc(OP_BF16, 128, 32), make_idesc(OP_BF16, 128, 64), make_idesc(OP_BF16, 128, 96),
+            make_idesc(OP_BF16, 128, 128), make_idesc(OP_BF16, 128, 160), make_idesc(OP_BF16, 128, 192),
+            make_idesc(OP_BF16, 128, 224), make_idesc(OP_BF16, 128, 256)};
         uint32_t f = ring0;
-        for (int h = 0; h < 2 && !oz_failed(os); ++h) {
-            const uint32_t u = half0 + h;
-            if (!mbar_wait(&os.bfull, u & 1, deadline)) {
+        for (int qq = 0; qq < kQuarters && !oz_failed(os); ++qq) {
+            const uint32_t u = q0 + qq, b = u & 1;
+            if (!mbar_wait(&os.bfull[b], (u >> 1) & 1, deadline)) {
                 oz_fail(os);
                 break;
             }
-            if (u > 0 && !mbar_wait(&os.tmem_empty, (u - 1) & 1, deadline)) {
+            // the epilogue of quarter u - 2 must have read this half of tensor memory
+            if (u >= 2 && !mbar_wait(&os.tmem_empty[b], ((u >> 1) - 1) & 1, deadline)) {
                 oz_fail(os);
                 break;
             }
             tc_fence_after();
-            // For A slice s, the products with B slices t = 0 .. 7-s go to groups
-            // g = s + t, whose accumulators sit at TMEM columns 64 g: contiguous.
-            // With the 8 B slices of a K-chunk stored as one 512-row operand, one
-            // MMA of N = 64 * (number of slices) covers up to 4 of them (N <= 256).
-            // Advancing K by 16 bf16 (32 bytes) adds 2 to the descriptor's
-            // start-address field (16-byte units).
-            const uint64_t bdesc0 = sdesc_sw128(smem_u32(sm.B[0]));
-            const uint64_t bdesc1 = sdesc_sw128(smem_u32(sm.B[kOzS]));
-            constexpr uint32_t kIdescN[5] = {0u, make_idesc(OP_BF16, 128, 64), make_idesc(OP_BF16, 128, 128),
-                                             make_idesc(OP_BF16, 128, 192), make_idesc(OP_BF16, 128, 256)};
+            const uint64_t bdesc[2] = {sdesc_sw128(smem_u32(sm.B[b][0])), sdesc_sw128(smem_u32(sm.B[b][kOzS]))};
+            const uint32_t dbase = os.tmem_base + b * (uint32_t)(kOzS * kOzQ);
             for (int s = 0; s < kOzS && !oz_failed(os); ++s)
                 for (int kc = 0; kc < 2; ++kc, ++f) {
                     const int st = (int)(f % kOzStages);
@@ -267,31 +279,25 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                     }
                     tc_fence_after();
                     const uint64_t adesc = sdesc_sw128(smem_u32(sm.A[st]));
-                    const uint64_t bd = kc ? bdesc1 : bdesc0;
-                    const int nt = kOzS - s;                 // slices t = 0 .. nt-1
-                    const int n1 = nt < 4 ? nt : 4;          // first MMA: t = 0 .. n1-1
-                    const uint32_t d1 = os.tmem_base + (uint32_t)(s * 64);
-                    const uint32_t d2 = os.tmem_base + (uint32_t)((s + 4) * 64);
-                    // B rows of slice 4 start 4 * 64 rows = 32 KB later: +2048 in 16-byte units
+                    const uint32_t idesc = kIdescN[kOzS - s];
+                    const uint32_t d = dbase + (uint32_t)(s * kOzQ);
 #pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4) {
-                        const uint32_t acc = (s == 0 && kc == 0 && k4 == 0) ? 0u : 1u;
-                        tc_mma<false>(d1, adesc + 2 * k4, bd + 2 * k4, kIdescN[n1], acc);
-                        if (nt > 4) tc_mma<false>(d2, adesc + 2 * k4, bd + 2048 + 2 * k4, kIdescN[nt - 4], acc);
-                    }
+                    for (int k4 = 0; k4 < 4; ++k4)
+                        tc_mma<false>(d, adesc + 2 * k4, bdesc[kc] + 2 * k4, idesc,
+                                      (s == 0 && kc == 0 && k4 == 0) ? 0u : 1u);
                     tc_commit(&os.empty[st]);
                 }
-            tc_commit(&os.acc_full);
-            tc_commit(&os.bfree);
+            tc_commit(&os.acc_full[b]);
+            tc_commit(&os.bfree[b]);
         }
     } else if (warp >= 4) {
         // ---------------- epilogue: 8 exact FP32 group sums -> binary64
         // G_g (d = g + 2) are integers below 2^24.  hi = sum_{g<4} G_g 2^{7(3-g)}
         // and lo = sum_{g>=4} G_g 2^{7(7-g)} are exact int64 (< 2^46); the
         // update is A B^T = 2^{e_r + e_c} (hi 2^-35 + lo 2^-63).  Each warp owns
-        // 32 rows; per 32-column chunk it stages its 32 x 32 block of C in shared
-        // memory with coalesced asynchronous copies, each lane (one row) applies
-        // its row's update there, and the block is written back coalesced.
+        // 32 rows; per quarter it stages its 32 x 32 block of C in shared memory
+        // with coalesced asynchronous copies, each lane (one row) applies its
+        // row's update there, and the block is written back coalesced.
         const int q = warp - 4;
         const int row = q * 32 + lane;
         // pull this row of C into L2 while the MMAs run (8 lines of 128 bytes)
@@ -305,99 +311,100 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
         asm volatile("bar.sync 1, 128;" ::: "memory");  // the 4 epilogue warps only
         const int ea = sm.ex[0][row];
         double *xp = sm.xp[q];
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t u = half0 + h;
-            if (!mbar_wait(&os.acc_full, u & 1, deadline)) {
+#pragma unroll 1
+        for (int qq = 0; qq < kQuarters; ++qq) {
+            const uint32_t u = q0 + qq, b = u & 1;
+            // stage this warp's 32 x 32 block of C in shared memory (async,
+            // coalesced 16-byte copies) while the accumulators are produced
+            double *cblk = C + (size_t)(q * 32) * kOzNb + qq * kOzQ;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int idx = i * 32 + lane, rr = idx >> 4, seg = idx & 15;
+                cp_async16(smem_u32(xp + xp_idx(rr, 2 * seg)), cblk + (size_t)rr * kOzNb + 2 * seg);
+            }
+            if (!mbar_wait(&os.acc_full[b], (u >> 1) & 1, deadline)) {
                 oz_fail(os);
+                cp_async_wait_all();
                 break;
             }
             tc_fence_after();
-#pragma unroll 1
-            for (int c = 0; c < 64; c += 32) {
-                // stage this warp's 32 x 32 block of C in shared memory (async,
-                // coalesced 16-byte copies) while the tensor-memory values are combined
-                double *cblk = C + (size_t)(q * 32) * kOzNb + h * 64 + c;
+            // group d = g + 2 holds at most d - 1 products below 2^21 each, so
+            // G_{2k} 128 + G_{2k+1} fits in int32; hi = (t01 << 14) + t23 and
+            // lo = (t45 << 14) + t67 are exact int64.
+            long long hi[32], lo[32];
+            const uint32_t tb = os.tmem_base + ((uint32_t)(q * 32) << 16) + b * (uint32_t)(kOzS * kOzQ);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int idx = i * 32 + lane, rr = idx >> 4, seg = idx & 15;
-                    cp_async16(smem_u32(xp + xp_idx(rr, 2 * seg)), cblk + (size_t)rr * kOzNb + 2 * seg);
-                }
-                // group d = g + 2 holds at most d - 1 products below 2^21 each, so
-                // G_{2k} 128 + G_{2k+1} fits in int32; hi = (t01 << 14) + t23 and
-                // lo = (t45 << 14) + t67 are exact int64.
-                long long hi[32], lo[32];
-                const uint32_t tb = os.tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)c;
+            for (int half4 = 0; half4 < 2; ++half4) {
+                int32_t t0[32], t1[32];
 #pragma unroll
-                for (int half4 = 0; half4 < 2; ++half4) {
-                    int32_t t0[32], t1[32];
-#pragma unroll
-                    for (int pr = 0; pr < 2; ++pr) {
-                        const int g = half4 * 4 + pr * 2;
-                        uint32_t ra[32], rb[32];
-                        tmem_ld32(tb + (uint32_t)(g * 64), ra);
-                        tmem_ld32(tb + (uint32_t)((g + 1) * 64), rb);
-                        tmem_ld_wait();
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int32_t v = __float2int_rn(__uint_as_float(ra[j])) * 128 +
-                                              __float2int_rn(__uint_as_float(rb[j]));
-                            if (pr == 0) t0[j] = v;
-                            else t1[j] = v;
-                        }
-                    }
+                for (int pr = 0; pr < 2; ++pr) {
+                    const int g = half4 * 4 + pr * 2;
+                    uint32_t ra[32], rb[32];
+                    tmem_ld32(tb + (uint32_t)(g * kOzQ), ra);
+                    tmem_ld32(tb + (uint32_t)((g + 1) * kOzQ), rb);
+                    tmem_ld_wait();
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const long long w = ((long long)t0[j] << 14) + (long long)t1[j];
-                        if (half4 == 0) hi[j] = w;
-                        else lo[j] = w;
+                        const int32_t v = __float2int_rn(__uint_as_float(ra[j])) * 128 +
+                                          __float2int_rn(__uint_as_float(rb[j]));
+                        if (pr == 0) t0[j] = v;
+                        else t1[j] = v;
                     }
                 }
-                // one vote per chunk: exponents of the scaled values stay normal
-                // (|hi|, |lo| < 2^47) unless a row or column scale is extreme
-                bool ok_range = true;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int eab = ea + sm.ex[1][h * 64 + c + j];
-                    ok_range &= (eab >= -900 && eab <= 900);
+                    const long long w = ((long long)t0[j] << 14) + (long long)t1[j];
+                    if (half4 == 0) hi[j] = w;
+                    else lo[j] = w;
                 }
-                cp_async_wait_all();
-                __syncwarp();
-                // this lane's row of the block: C <- (C - hi 2^(eab-35)) - lo 2^(eab-63)
-                if (__all_sync(0xffffffffu, ok_range)) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int eab = ea + sm.ex[1][h * 64 + c + j];
-                        double &cv = xp[xp_idx(lane, j)];
-                        cv = (cv - int_scaled_fast(hi[j], eab - 35)) - int_scaled_fast(lo[j], eab - 63);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int eab = ea + sm.ex[1][h * 64 + c + j];
-                        double &cv = xp[xp_idx(lane, j)];
-                        cv = (cv - int_scaled(hi[j], eab - 35)) - int_scaled(lo[j], eab - 63);
-                    }
-                }
-                __syncwarp();
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int idx = i * 32 + lane, rr = idx >> 4, seg = idx & 15;
-                    const double2 v = *reinterpret_cast<const double2 *>(xp + xp_idx(rr, 2 * seg));
-                    *reinterpret_cast<double2 *>(cblk + (size_t)rr * kOzNb + 2 * seg) = v;
-                }
-                __syncwarp();
             }
+            // the accumulators are in registers: release this half of tensor
+            // memory to the MMAs of quarter u + 2 before updating C
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&os.tmem_empty);
+            if (lane == 0) mbar_arrive(&os.tmem_empty[b]);
+            // one vote per quarter: exponents of the scaled values stay normal
+            // (|hi|, |lo| < 2^47) unless a row or column scale is extreme
+            bool ok_range = true;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int eab = ea + sm.ex[1][qq * kOzQ + j];
+                ok_range &= (eab >= -900 && eab <= 900);
+            }
+            cp_async_wait_all();
+            __syncwarp();
+            // this lane's row of the block: C <- (C - hi 2^(eab-35)) - lo 2^(eab-63)
+            if (__all_sync(0xffffffffu, ok_range)) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int eab = ea + sm.ex[1][qq * kOzQ + j];
+                    double &cv = xp[xp_idx(lane, j)];
+                    cv = (cv - int_scaled_fast(hi[j], eab - 35)) - int_scaled_fast(lo[j], eab - 63);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int eab = ea + sm.ex[1][qq * kOzQ + j];
+                    double &cv = xp[xp_idx(lane, j)];
+                    cv = (cv - int_scaled(hi[j], eab - 35)) - int_scaled(lo[j], eab - 63);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int idx = i * 32 + lane, rr = idx >> 4, seg = idx & 15;
+                const double2 v = *reinterpret_cast<const double2 *>(xp + xp_idx(rr, 2 * seg));
+                *reinterpret_cast<double2 *>(cblk + (size_t)rr * kOzNb + 2 * seg) = v;
+            }
+            __syncwarp();
         }
     }
     __syncthreads();
     const bool ok = !oz_failed(os);
     __syncthreads();
     if (threadIdx.x == 0 && ok) {
-        os.ring = ring0 + 2 * kOzS * 2;
-        os.halves = half0 + 2;
+        os.ring = ring0 + kQuarters * kOzS * 2;
+        os.quarters = q0 + kQuarters;
     }
     __syncthreads();
     return ok;
