@@ -85,7 +85,7 @@ typedef enum {
 /* opts->flags */
 enum {
     CHOL_FLAG_NOOP = 1,          /* replace every tile kernel body by a no-op (Section 4.2 overhead runs) */
-    CHOL_FLAG_PRIORITY = 2,      /* dataflow: POTRF, TRSM, SYRK and the GEMMs updating the next 4 panel columns
+    CHOL_FLAG_PRIORITY = 2,      /* dataflow: POTRF, TRSM, SYRK and the GEMMs updating the next 16 panel columns
                                     before the other GEMMs (OpenMP 4.5 priorities analog) */
     CHOL_FLAG_GRAPH = 4,         /* fork-join: replay the per-step launches from a cached CUDA graph */
     CHOL_FLAG_TEST_WITHHOLD = 8, /* dataflow test hook: never release the last POTRF, so the

@@ -300,52 +300,47 @@ __device__ __forceinline__ void df_push(Control *ctl, const DFArgs &d, int q, ui
 // Pop one task (thread 0).  Returns 1 (task in *out), 0 (all tasks done) or
 // -1 (abort, failure elsewhere, or a wait longer than the timeout).
 //
-// The priority queue is popped by compare-and-swap on its head (few tasks,
-// short bursts).  The normal queue is popped by ticket: a CTA takes the next
-// slot index with one fetch-and-add and keeps it (*ticket) until a push fills
-// that slot, checking the priority queue meanwhile; there is no retry storm on
-// a contended head.  Slots are handed out in push order, so the queue stays
-// FIFO; a ticket past the last normal task is never filled and is dropped
-// when every task has completed.
+// Both queues are popped by ticket: a CTA takes the next slot index of a
+// queue with one fetch-and-add and keeps it (tk[q]) until a push fills that
+// slot -- no compare-and-swap retry storm on a contended head.  A CTA holds
+// at most one ticket per queue; it claims a priority ticket only when the
+// priority queue has unclaimed entries, serves a filled priority slot first,
+// and runs normal tasks while its priority ticket is still unfilled.  Slots
+// are handed out in push order, so each queue stays FIFO; a ticket past the
+// last push is never filled and is dropped when every task has completed.
 constexpr unsigned long long kNoTicket = ~0ull;
-constexpr int kLookahead = 4;  // panel columns ahead whose updates are prioritized
+constexpr int kLookahead = 16;  // panel columns ahead whose updates are prioritized
 
-static __device__ int df_pop(Control *ctl, const DFArgs &d, uint64_t *out, unsigned long long *ticket) {
+static __device__ int df_pop(Control *ctl, const DFArgs &d, uint64_t *out, unsigned long long *tk) {
     const uint64_t t0 = global_ns();
+    const unsigned long long cap = (unsigned long long)d.capacity;
     uint32_t backoff = 32;
     for (;;) {
         // independent loads, issued together (one round trip to L2)
         const int32_t ab = ld_acquire_s32(&ctl->abort);
         const unsigned long long done = ld_relaxed_u64(&ctl->completed);
         const unsigned long long h = ld_relaxed_u64(&ctl->head[0]);
-        const unsigned long long t = ld_acquire_u64(&ctl->tail[0]);
-        const bool have = *ticket < (unsigned long long)d.capacity;
-        const uint64_t v = have ? ld_acquire_u64(&d.queue[(size_t)d.capacity + *ticket]) : kEmptySlot;
+        const unsigned long long t = ld_relaxed_u64(&ctl->tail[0]);
+        const uint64_t vp = tk[0] < cap ? ld_acquire_u64(&d.queue[tk[0]]) : kEmptySlot;
+        const uint64_t vn = tk[1] < cap ? ld_acquire_u64(&d.queue[cap + tk[1]]) : kEmptySlot;
         if (ab) return -1;
         if (done >= (uint64_t)d.total) return 0;
-        if (h < t) {
-            if (atomicCAS(&ctl->head[0], h, h + 1) == h) {
-                const unsigned long long *slot = &d.queue[h];
-                uint64_t w;
-                // the pusher reserved this slot before we saw it: it is written shortly
-                while ((w = ld_acquire_u64(slot)) == kEmptySlot) {
-                    if (global_ns() - t0 > d.timeout_ns) {
-                        df_timeout(ctl, 2);
-                        return -1;
-                    }
-                }
-                *out = w;
-                return 1;
-            }
-            continue;  // lost the race for this slot: look again at once
-        }
-        if (v != kEmptySlot) {
-            *ticket = kNoTicket;
-            *out = v;
+        if (vp != kEmptySlot) {
+            tk[0] = kNoTicket;
+            *out = vp;
             return 1;
         }
-        if (*ticket == kNoTicket) {
-            *ticket = atomicAdd(&ctl->head[1], 1ull);
+        if (tk[0] == kNoTicket && h < t) {
+            tk[0] = atomicAdd(&ctl->head[0], 1ull);
+            continue;
+        }
+        if (vn != kEmptySlot) {
+            tk[1] = kNoTicket;
+            *out = vn;
+            return 1;
+        }
+        if (tk[1] == kNoTicket) {
+            tk[1] = atomicAdd(&ctl->head[1], 1ull);
             continue;
         }
         if (global_ns() - t0 > d.timeout_ns) {
@@ -415,7 +410,7 @@ __global__ void __launch_bounds__(256) df_kernel(const __grid_constant__ typenam
     __shared__ int s_cmd;
     Control *ctl = a.ctl;
     Body::cta_init(g, sm);
-    unsigned long long ticket = kNoTicket;  // thread 0: claimed slot of the normal queue
+    unsigned long long tk[2] = {kNoTicket, kNoTicket};  // thread 0: claimed slots (priority, normal)
     uint64_t cont = kEmptySlot;             // thread 0: ready chain successor of the last task
     for (;;) {
         if (threadIdx.x == 0) {
@@ -441,7 +436,7 @@ __global__ void __launch_bounds__(256) df_kernel(const __grid_constant__ typenam
                 }
                 cont = kEmptySlot;
             }
-            if (cmd == 0) cmd = df_pop(ctl, d, &v, &ticket);
+            if (cmd == 0) cmd = df_pop(ctl, d, &v, tk);
             if (cmd == 1) fence_acq_rel();
             s_task = v;
             s_cmd = cmd;

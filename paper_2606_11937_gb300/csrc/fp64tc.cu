@@ -1,7 +1,10 @@
 // fp64tc.cu -- FP64 factorization whose SYRK/GEMM run on the tensor cores with
-// binary64 accuracy (exact bf16 slicing, ozaki.cuh); POTRF and TRSM stay on
-// the CUDA cores in binary64.  Selected with CHOL_FLAG_FP64_TC; tiles of order
-// 128.  Both schedules of Section 3.2 run this body unchanged.
+// binary64 accuracy (exact bf16 slicing, ozaki.cuh).  POTRF stays on the CUDA
+// cores in binary64 and also forms W_J = L_JJ^{-1} by substitution; the TRSMs
+// of block column J are then one emulated product A_IJ W_J^T each on the
+// tensor cores, unless L_JJ is ill-conditioned (kappa_inf above kTrsmKappa),
+// when they keep the substitution kernel.  Selected with CHOL_FLAG_FP64_TC;
+// tiles of order 128.  Both schedules of Section 3.2 run this body unchanged.
 #include <cuda.h>
 #include <string.h>
 
@@ -21,11 +24,51 @@ static int make_slice_map(CUtensorMap *map, void *base, int64_t rows, int box_ro
 struct OzArgs {
     CUtensorMap mapA;   // slice store, 128-row boxes
     CUtensorMap mapB;   // slice store, 32-row boxes (one quarter of a tile)
+    CUtensorMap mapW;   // slices of the inverted diagonal tiles, 32-row boxes
     TileStore<double> S;
     __nv_bfloat16 *slices;  // per tile: 8 slices of 128 x 128
     int32_t *rexp;          // per tile: 128 row exponents
+    __nv_bfloat16 *wslices; // per block column J: 8 slices of W_J = L_JJ^{-1}
+    int32_t *wexp;          // per block column J: 128 row exponents of W_J
+    double *wbuf;           // per block column J: L_JJ^{-T} in binary64 (row-major)
+    int32_t *wflag;         // per block column J: 1 if its TRSMs use W_J (kappa_inf(L_JJ) <= kTrsmKappa)
     uint64_t timeout_ns;
 };
+
+// Largest infinity-norm condition number ||L_JJ|| ||L_JJ^{-1}|| for which the
+// TRSMs of block column J multiply by the inverse (the error of X W^T grows
+// with it); a worse-conditioned diagonal tile keeps the substitution TRSM.
+constexpr double kTrsmKappa = 65536.0;
+
+// kappa_inf(L) = max_r sum_c |L_rc| * max_c sum_r |Y_rc| for the lower
+// triangular L and Y = L^{-T} (row sums of L^{-1} are column sums of Y).
+// All threads; the result is valid in every thread.
+__device__ double oz_kappa_inf(const double *L, const double *Y, double *red) {
+    double mL = 0.0, mY = 0.0;
+    for (int i = threadIdx.x; i < kOzNb; i += kThreads) {
+        double sl = 0.0, sy = 0.0;
+        for (int c = 0; c <= i; ++c) sl += fabs(__ldcg(L + (size_t)i * kOzNb + c));
+        for (int r = 0; r <= i; ++r) sy += fabs(__ldcg(Y + (size_t)r * kOzNb + i));
+        mL = fmax(mL, sl);
+        mY = fmax(mY, sy);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mL = fmax(mL, __shfl_xor_sync(0xffffffffu, mL, o));
+        mY = fmax(mY, __shfl_xor_sync(0xffffffffu, mY, o));
+    }
+    if (threadIdx.x % 32 == 0) {
+        red[threadIdx.x / 32] = mL;
+        red[8 + threadIdx.x / 32] = mY;
+    }
+    __syncthreads();
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+        a = fmax(a, red[w]);
+        b = fmax(b, red[8 + w]);
+    }
+    __syncthreads();
+    return a * b;
+}
 
 struct OzBody {
     using Args = OzArgs;
@@ -48,15 +91,54 @@ struct OzBody {
             switch (type) {
             case T_POTRF: {
                 const int li = tile_potrf(S.tile(J, J), kOzNb, ss);
-                if (li && threadIdx.x == 0) {
-                    report_info(a.ctl, (int64_t)J * kOzNb + li);
-                    st_release_s32(&a.ctl->abort, 1);
+                if (li) {
+                    if (threadIdx.x == 0) {
+                        report_info(a.ctl, (int64_t)J * kOzNb + li);
+                        st_release_s32(&a.ctl->abort, 1);
+                    }
+                } else if (J < S.M - 1) {
+                    // W_J = L_JJ^{-1} for the TRSMs of this block column:
+                    // Y = I L_JJ^{-T} by the substitution kernel, then the
+                    // slices of W_J = Y^T (rows of W_J are the columns of Y)
+                    double *Y = g.wbuf + (size_t)J * kOzNb * kOzNb;
+                    for (int e = threadIdx.x; e < kOzNb * kOzNb; e += kThreads)
+                        Y[e] = (e / kOzNb == e % kOzNb) ? 1.0 : 0.0;
+                    __syncthreads();
+                    tile_trsm(Y, S.tile(J, J), kOzNb, ss, true);
+                    const double kappa = oz_kappa_inf(S.tile(J, J), Y, sm.xp[0]);
+                    const bool use_w = kappa <= kTrsmKappa;  // false also for a NaN
+                    if (use_w)
+                        ozaki_split(Y, g.wslices + (size_t)J * kOzS * kOzNb * kOzNb, g.wexp + (size_t)J * kOzNb,
+                                    false, true);
+                    if (threadIdx.x == 0) g.wflag[J] = use_w ? 1 : 0;
                 }
             } break;
             case T_TRSM: {
-                tile_trsm(S.tile(I, J), S.tile(J, J), kOzNb, ss);
+                if (!__ldcg(g.wflag + J)) {  // substitution on the CUDA cores
+                    tile_trsm(S.tile(I, J), S.tile(J, J), kOzNb, ss);
+                    const int64_t t = tile_index(I, J);
+                    ozaki_split(S.tile(I, J), g.slices + (size_t)t * kOzS * kOzNb * kOzNb, g.rexp + t * kOzNb);
+                    break;
+                }
+                // A_IJ L_JJ^{-T} = A_IJ W_J^T on the tensor cores: the slices of
+                // -A_IJ go to this tile's slice slot, the tile is cleared, the
+                // emulated update C -= (-A_IJ) W_J^T leaves the solution in it,
+                // and the solution's own slices replace those of -A_IJ.
                 const int64_t t = tile_index(I, J);
-                ozaki_split(S.tile(I, J), g.slices + (size_t)t * kOzS * kOzNb * kOzNb, g.rexp + t * kOzNb);
+                double *X = S.tile(I, J);
+                __nv_bfloat16 *sl = g.slices + (size_t)t * kOzS * kOzNb * kOzNb;
+                ozaki_split(X, sl, g.rexp + t * kOzNb, true, false);
+                for (int e = threadIdx.x; e < kOzNb * kOzNb; e += kThreads) X[e] = 0.0;
+                __syncthreads();
+                const bool ok = ozaki_tile_update(sm, &g.mapA, &g.mapW, X, (int)(t * kOzS * kOzNb),
+                                                  (int)((int64_t)J * kOzS * kOzNb), g.rexp + t * kOzNb,
+                                                  g.wexp + (size_t)J * kOzNb, g.timeout_ns);
+                if (ok) {
+                    ozaki_split(X, sl, g.rexp + t * kOzNb);
+                } else if (threadIdx.x == 0) {
+                    if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 4;
+                    st_release_s32(&a.ctl->abort, 1);
+                }
             } break;
             default: {
                 const int64_t ta = tile_index(I, J), tb = tile_index(K, J);
@@ -81,7 +163,10 @@ static size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 // Workspace bytes beyond the FP64 tile store for an order-n factorization.
 size_t fp64tc_extra_bytes(int64_t n) {
     const int64_t M = (n + kOzNb - 1) / kOzNb;
-    return a256((size_t)num_tiles(M) * kOzS * kOzNb * kOzNb * 2) + a256((size_t)num_tiles(M) * kOzNb * 4);
+    const size_t tiles = (size_t)num_tiles(M);
+    return a256(tiles * kOzS * kOzNb * kOzNb * 2) + a256(tiles * kOzNb * 4) +   // tile slices, exponents
+           a256((size_t)M * kOzS * kOzNb * kOzNb * 2) + a256((size_t)M * kOzNb * 4) +  // W_J slices, exponents
+           a256((size_t)M * kOzNb * kOzNb * 8) + a256((size_t)M * 4);               // L_JJ^{-T}, flags
 }
 
 // Run the schedule with the tensor-core FP64 body on a repacked tile store.
@@ -97,10 +182,20 @@ int fp64tc_schedule(double *store, int64_t n, Control *ctl, unsigned long long *
     memset(&g, 0, sizeof(g));
     g.S = TileStore<double>{store, kOzNb, (int32_t)M};
     g.slices = (__nv_bfloat16 *)ws;
-    g.rexp = (int32_t *)((char *)ws + b_sl);
+    char *p = (char *)ws + b_sl;
+    g.rexp = (int32_t *)p;
+    p += a256((size_t)tiles * kOzNb * 4);
+    g.wslices = (__nv_bfloat16 *)p;
+    p += a256((size_t)M * kOzS * kOzNb * kOzNb * 2);
+    g.wexp = (int32_t *)p;
+    p += a256((size_t)M * kOzNb * 4);
+    g.wbuf = (double *)p;
+    p += a256((size_t)M * kOzNb * kOzNb * 8);
+    g.wflag = (int32_t *)p;
     g.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
     int rc = make_slice_map(&g.mapA, g.slices, tiles * kOzS * kOzNb, 128);
     if (rc == CHOL_OK) rc = make_slice_map(&g.mapB, g.slices, tiles * kOzS * kOzNb, kOzQ);
+    if (rc == CHOL_OK) rc = make_slice_map(&g.mapW, g.wslices, M * kOzS * kOzNb, kOzQ);
     SchedArgs a{ctl, o.trace, o.trace_capacity, o.flags, 0};
     if (rc == CHOL_OK) {
         if (sched == CHOL_SCHED_DATAFLOW) {

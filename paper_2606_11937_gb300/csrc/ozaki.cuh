@@ -76,13 +76,15 @@ __device__ __forceinline__ uint16_t small_int_bf16(uint32_t a, uint32_t neg) {
     return (uint16_t)((neg << 15) | ((127u + msb) << 7) | mant);
 }
 
-// Split a row-major 128 x 128 binary64 tile into 8 bf16 slices ([s][r][c],
-// 32 KB each) and one exponent per row.  With x = v 2^-e in (-1, 1) and
+// Split a 128 x 128 binary64 tile into 8 bf16 slices ([s][r][c], 32 KB each)
+// and one exponent per row.  With x = v 2^-e in (-1, 1) and
 // X = floor(|x| 2^56), slice s (1-based) is sign(x) times bits
 // [56 - 7s, 63 - 7s) of X -- the digits the recursion t = 128 x,
 // a = trunc(t), x = t - a produces -- computed with integer operations on
-// the binary64 encoding.  All 256 threads; ends with a barrier.
-__device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32_t *rexp) {
+// the binary64 encoding.  Element (r, c) is T[r * 128 + c], or T[c * 128 + r]
+// with `transpose`; `negate` splits -T.  All 256 threads; ends with a barrier.
+__device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32_t *rexp, bool negate = false,
+                                   bool transpose = false) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     uint16_t *out = reinterpret_cast<uint16_t *>(slices);
     for (int r = warp; r < kOzNb; r += 8) {
@@ -90,7 +92,8 @@ __device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32
         double m = 0.0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            v[q] = __ldcg(T + (size_t)r * kOzNb + lane + 32 * q);
+            const int c = lane + 32 * q;
+            v[q] = __ldcg(T + (transpose ? (size_t)c * kOzNb + r : (size_t)r * kOzNb + c));
             m = fmax(m, fabs(v[q]));
         }
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -100,7 +103,7 @@ __device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const unsigned long long bits = (unsigned long long)__double_as_longlong(v[q]);
-            const uint32_t neg = (uint32_t)(bits >> 63);
+            const uint32_t neg = (uint32_t)(bits >> 63) ^ (negate ? 1u : 0u);
             const int expo = (int)((bits >> 52) & 0x7FF);
             unsigned long long M = bits & ((1ull << 52) - 1);
             int qexp;                      // |v| = M 2^qexp

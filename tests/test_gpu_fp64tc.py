@@ -10,7 +10,11 @@ binary64 accuracy from exact bf16 slicing.
   rounded binary64 additions) plus one rounding of the result;
 * the factorization meets the same FP64 parity bar as the DFMA path
   (scaled error <= 1e-11 vs the oracle, residual <= 1e-14 sqrt(n)), is exact
-  on Pascal and integer inputs, and the schedules agree bit for bit.
+  on Pascal and integer inputs, and the schedules agree bit for bit;
+* TRSMs multiply by the inverted diagonal tile on the tensor cores when it is
+  well conditioned (the SE and Gram inputs: kappa_inf of every diagonal tile
+  below 500), and keep the substitution kernel otherwise (the integer factors,
+  kappa_inf ~ 1e12, which therefore stay exact).
 """
 import math
 
@@ -112,3 +116,22 @@ def test_fp64tc_non_spd_info():
     for sched in ("dataflow", "fork_join"):
         _, info, _, rc = gpu_factor(A, schedule=sched, flags=chol.CHOL_FLAG_FP64_TC)
         assert rc == 0 and info == want
+
+
+@pytest.mark.parametrize("nugget", [1e-2, 1e-3])
+def test_fp64tc_inverse_trsm_parity(nugget):
+    """SE covariance, ragged n: the TRSMs take the inverse path; FP64 parity
+    bar against the oracle, residual bound, and bitwise agreement of the two
+    schedules."""
+    import paper_2606_11937_gb300 as chol
+    n = 1500
+    S = matrix("se", n, 5, nugget)
+    Lref, _ = oracle_factor("se", n, 5, nugget)
+    outs = []
+    for sched in ("dataflow", "fork_join"):
+        L, info, _, rc = gpu_factor(S, schedule=sched, flags=chol.CHOL_FLAG_FP64_TC | chol.CHOL_FLAG_PRIORITY)
+        assert rc == 0 and info == 0
+        assert scaled_error(L, Lref, S) <= TOL_SCALED
+        assert probe_residual(S, L) <= resid_bound(n)
+        outs.append(L)
+    assert np.array_equal(outs[0], outs[1])
