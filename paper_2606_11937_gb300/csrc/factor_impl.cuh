@@ -28,12 +28,15 @@ struct TileStore {
     }
 };
 
+struct DFLocal;
+
 struct SchedArgs {
     Control *ctl;
     chol_trace_rec *trace;
     int64_t trace_cap;
     int32_t flags;
     int32_t pad;
+    DFLocal *dfl;  // dataflow kernel: this CTA's scheduler state (shared memory); else null
 };
 
 struct DFArgs {
@@ -44,6 +47,14 @@ struct DFArgs {
     uint64_t timeout_ns;
     int32_t num_matrices;
     int32_t pad;
+};
+
+// Per-CTA scheduler state of the dataflow kernel, in shared memory and used
+// by thread 0 only: the claimed queue slots and a task taken ahead of time.
+struct DFLocal {
+    DFArgs d;
+    unsigned long long tk[2];  // claimed slots (priority, normal), or kNoTicket
+    uint64_t next;             // a ready task held for the next iteration, or kEmptySlot
 };
 
 constexpr int kSolveJ = 0xFFFF;  // J marker of the fused SOLVE task (batched)
@@ -352,6 +363,40 @@ static __device__ int df_pop(Control *ctl, const DFArgs &d, uint64_t *out, unsig
     }
 }
 
+// One non-blocking attempt (thread 0): take a filled claimed slot, or claim
+// a slot for later.  True with the task in *out.
+static __device__ bool df_try_pop(Control *ctl, DFLocal &L, uint64_t *out) {
+    const unsigned long long cap = (unsigned long long)L.d.capacity;
+    const unsigned long long h = ld_relaxed_u64(&ctl->head[0]);
+    const unsigned long long t = ld_relaxed_u64(&ctl->tail[0]);
+    const uint64_t vp = L.tk[0] < cap ? ld_acquire_u64(&L.d.queue[L.tk[0]]) : kEmptySlot;
+    const uint64_t vn = L.tk[1] < cap ? ld_acquire_u64(&L.d.queue[cap + L.tk[1]]) : kEmptySlot;
+    if (vp != kEmptySlot) {
+        L.tk[0] = kNoTicket;
+        *out = vp;
+        return true;
+    }
+    if (L.tk[0] == kNoTicket && h < t) L.tk[0] = atomicAdd(&ctl->head[0], 1ull);
+    if (vn != kEmptySlot) {
+        L.tk[1] = kNoTicket;
+        *out = vn;
+        return true;
+    }
+    if (L.tk[1] == kNoTicket) L.tk[1] = atomicAdd(&ctl->head[1], 1ull);
+    return false;
+}
+
+// Called by a body's thread 0 while it has nothing else to do inside a task
+// (the TMA producer after its last load): take the next task ahead of time,
+// so that the queue round trips overlap the task.  No-op outside the
+// dataflow kernel or when a task is already held.
+__device__ __forceinline__ void df_take_ahead(const SchedArgs &a) {
+    if (a.dfl && a.dfl->next == kEmptySlot) {
+        uint64_t v;
+        if (df_try_pop(a.ctl, *a.dfl, &v)) a.dfl->next = v;
+    }
+}
+
 // Priority class (with CHOL_FLAG_PRIORITY): the tasks that lead to the next
 // POTRFs -- POTRF, TRSM, SYRK and the GEMMs that update one of the next
 // kLookahead panel columns (K <= J + kLookahead).
@@ -404,39 +449,61 @@ __device__ void df_notify(const typename Body::Args &g, const SchedArgs &a, cons
 }
 
 template <class Body>
-__global__ void __launch_bounds__(256) df_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a, DFArgs d) {
+__global__ void __launch_bounds__(256) df_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a0,
+                                                 DFArgs d) {
     typename Body::Smem &sm = body_smem<Body>();
     __shared__ unsigned long long s_task;
     __shared__ int s_cmd;
-    Control *ctl = a.ctl;
+    __shared__ DFLocal s_local;
+    Control *ctl = a0.ctl;
+    SchedArgs a = a0;
+    a.dfl = &s_local;
+    if (threadIdx.x == 0) {
+        s_local.d = d;
+        s_local.tk[0] = s_local.tk[1] = kNoTicket;
+        s_local.next = kEmptySlot;
+    }
     Body::cta_init(g, sm);
-    unsigned long long tk[2] = {kNoTicket, kNoTicket};  // thread 0: claimed slots (priority, normal)
-    uint64_t cont = kEmptySlot;             // thread 0: ready chain successor of the last task
+    uint64_t cont = kEmptySlot;  // thread 0: ready chain successor of the last task
+    int32_t aborted = 0;         // thread 0: abort flag seen after the last task
     for (;;) {
         if (threadIdx.x == 0) {
             uint64_t v = 0;
             int cmd = 0;
-            if (cont != kEmptySlot) {
-                // run the chain successor here, unless it is a normal-class task
-                // and priority work is waiting: then it goes to the normal queue
-                const int cj = (int)(cont & 0xffff), ck = (int)((cont >> 16) & 0xffff);
-                const int ci = (int)((cont >> 32) & 0xffff);
-                bool run_here = true;
-                if ((a.flags & CHOL_FLAG_PRIORITY) && !df_is_priority(a.flags, ci, ck, cj)) {
+            DFLocal &L = s_local;
+            if (aborted) {
+                cmd = -1;
+            } else if (L.next != kEmptySlot || cont != kEmptySlot) {
+                // a task held from a take-ahead and/or the chain successor: run a
+                // priority-class one first, else the chain successor (its tile is
+                // hot in L2), and hold the other for the next iteration
+                uint64_t pick = cont, keep = L.next;
+                if (pick == kEmptySlot || (keep != kEmptySlot && df_is_priority(a.flags, (int)((keep >> 32) & 0xffff),
+                                                                              (int)((keep >> 16) & 0xffff),
+                                                                              (int)(keep & 0xffff)) &&
+                                           !df_is_priority(a.flags, (int)((pick >> 32) & 0xffff),
+                                                           (int)((pick >> 16) & 0xffff), (int)(pick & 0xffff)))) {
+                    pick = L.next;
+                    keep = cont;
+                }
+                L.next = keep;
+                cont = kEmptySlot;
+                cmd = 1;
+                v = pick;
+                // a normal-class chain successor, nothing held, priority work
+                // waiting: the successor goes to the normal queue
+                if (keep == kEmptySlot && (a.flags & CHOL_FLAG_PRIORITY) &&
+                    !df_is_priority(a.flags, (int)((pick >> 32) & 0xffff), (int)((pick >> 16) & 0xffff),
+                                    (int)(pick & 0xffff))) {
                     const unsigned long long h = ld_relaxed_u64(&ctl->head[0]);
-                    const unsigned long long t = ld_acquire_u64(&ctl->tail[0]);
+                    const unsigned long long t = ld_relaxed_u64(&ctl->tail[0]);
                     if (h < t) {
-                        df_push(ctl, d, 1, cont);
-                        run_here = false;
+                        df_push(ctl, d, 1, pick);
+                        cmd = 0;
                     }
                 }
-                if (run_here) {
-                    cmd = ld_acquire_s32(&ctl->abort) ? -1 : 1;
-                    v = cont;
-                }
-                cont = kEmptySlot;
             }
-            if (cmd == 0) cmd = df_pop(ctl, d, &v, tk);
+            if (cmd == 0) cmd = df_pop(ctl, d, &v, L.tk);
             if (cmd == 1) fence_acq_rel();
             s_task = v;
             s_cmd = cmd;
@@ -454,12 +521,19 @@ __global__ void __launch_bounds__(256) df_kernel(const __grid_constant__ typenam
             Body::run(g, a, m, I, K, J, sm);   // ends with __syncthreads()
         }
         if (threadIdx.x < 32) {
-            fence_acq_rel();                   // publish this CTA's tile writes (cumulative after the barrier)
+            // No separate fence: every way a successor is published is a
+            // release at GPU scope (the acq_rel counter update, the release
+            // store of a queue slot) by a warp-0 thread that passed the
+            // barrier ending the task, so the CTA's tile writes are ordered
+            // before it.
             __syncwarp();
-            if (J != kSolveJ && !ld_relaxed_s32(&ctl->abort))
-                df_notify<Body>(g, a, d, m, I, K, J, threadIdx.x, &cont);
+            const int32_t ab = ld_relaxed_s32(&ctl->abort);
+            if (J != kSolveJ && !ab) df_notify<Body>(g, a, d, m, I, K, J, threadIdx.x, &cont);
             __syncwarp();
-            if (threadIdx.x == 0) atomicAdd(&ctl->completed, 1ull);
+            if (threadIdx.x == 0) {
+                atomicAdd(&ctl->completed, 1ull);
+                aborted = ab;
+            }
         }
     }
     Body::cta_fini(g, sm);

@@ -87,6 +87,9 @@ struct OzBody {
         if (a.trace && threadIdx.x == 0) t0 = global_ns();
         const TileStore<double> &S = g.S;
         SimtSmem<double> &ss = *reinterpret_cast<SimtSmem<double> *>(sm.B);
+        // the TMA producer (thread 0) takes the next task from the queues once
+        // its loads are issued, while the tensor cores and the epilogue finish
+        const auto take_ahead = [&a]() { df_take_ahead(a); };
         if (!(a.flags & CHOL_FLAG_NOOP)) {
             switch (type) {
             case T_POTRF: {
@@ -132,7 +135,7 @@ struct OzBody {
                 __syncthreads();
                 const bool ok = ozaki_tile_update(sm, &g.mapA, &g.mapW, X, (int)(t * kOzS * kOzNb),
                                                   (int)((int64_t)J * kOzS * kOzNb), g.rexp + t * kOzNb,
-                                                  g.wexp + (size_t)J * kOzNb, g.timeout_ns);
+                                                  g.wexp + (size_t)J * kOzNb, g.timeout_ns, take_ahead);
                 if (ok) {
                     ozaki_split(X, sl, g.rexp + t * kOzNb);
                 } else if (threadIdx.x == 0) {
@@ -144,7 +147,7 @@ struct OzBody {
                 const int64_t ta = tile_index(I, J), tb = tile_index(K, J);
                 const bool ok = ozaki_tile_update(sm, &g.mapA, &g.mapB, S.tile(I, K), (int)(ta * kOzS * kOzNb),
                                                   (int)(tb * kOzS * kOzNb), g.rexp + ta * kOzNb,
-                                                  g.rexp + tb * kOzNb, g.timeout_ns);
+                                                  g.rexp + tb * kOzNb, g.timeout_ns, take_ahead);
                 if (!ok && threadIdx.x == 0) {
                     if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 4;
                     st_release_s32(&a.ctl->abort, 1);

@@ -559,8 +559,16 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
             break;
         }
         for (it = 0;; ++it) {
-            // r = b - A x (FP64) and the backward error
-            residual_kernel<<<dim3(nblk, ny), 256, 0, st>>>(h->A, h->lda, n, X, ldx, B, ldb, R, n, nrhs);
+            // r = b - A x (FP64) and the backward error (x = 0 at the start: r = b)
+            if (it == 0) {
+                if (cudaMemcpy2DAsync(R, n * 8, B, ldb * 8, n * 8, nrhs, cudaMemcpyDeviceToDevice, st) !=
+                    cudaSuccess) {
+                    rc = cuda_fail(cudaGetLastError(), "refinement", __FILE__, __LINE__);
+                    break;
+                }
+            } else {
+                residual_kernel<<<dim3(nblk, ny), 256, 0, st>>>(h->A, h->lda, n, X, ldx, B, ldb, R, n, nrhs);
+            }
             if (cudaMemsetAsync(mx, 0, 3 * nrhs * 8, st) != cudaSuccess) { rc = CHOL_ERR_CUDA; break; }
             colmax_kernel<<<vgrid, 256, 0, st>>>(R, n, X, ldx, B, ldb, n, nrhs, mx);
             if (cudaMemcpyAsync(hm.data(), mx, 3 * nrhs * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -209,9 +209,15 @@ inline __device__ void oz_cta_fini(OzShared &os) {
 //
 // Quarter u (counted across tasks) uses B buffer and tensor-memory half
 // b = u & 1; the k-th use of a buffer waits on its barriers with parity k & 1.
+// The producer thread (thread 0) calls producer_idle() after its last load.
+struct OzNoHook {
+    __device__ void operator()() const {}
+};
+
+template <class Hook = OzNoHook>
 __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, const CUtensorMap *mapB, double *C,
                                          int aRow0, int bRow0, const int32_t *expA, const int32_t *expB,
-                                         uint64_t timeout_ns) {
+                                         uint64_t timeout_ns, const Hook &producer_idle = Hook()) {
     OzShared &os = sm.os;
     const uint32_t ring0 = os.ring, q0 = os.quarters;
     const uint64_t deadline = global_ns() + timeout_ns;
@@ -246,6 +252,7 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                     tma_load_2d(smem_u32(sm.A[st]), mapA, &os.full[st], kc * 64, aRow0 + s * 128);
                 }
         }
+        producer_idle();
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         // For A slice s, the products with B slices t = 0 .. 7-s go to groups

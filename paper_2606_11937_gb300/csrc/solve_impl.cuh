@@ -6,7 +6,9 @@
 // ticket order, so it only ever waits for blocks owned by CTAs that started
 // before it (no deadlock whatever the residency).  It accumulates the
 // contributions of the finished blocks as their ready flags appear (acquire),
-// solves its diagonal block, stores the result and releases its own flag.
+// solves its diagonal block (loaded before the waits; one warp per pair of
+// right-hand sides, shuffles instead of block barriers), stores the result
+// and releases its own flag.
 // Every wait is bounded by a %globaltimer deadline after which the kernel
 // records CHOL_ERR_TIMEOUT and returns.  grid.y splits the right-hand sides
 // into slices of kRC columns, each with its own tickets and flags.
@@ -47,10 +49,74 @@ struct SolveCtl {
 
 template <typename T>
 struct SolveSmem {
-    T Ls[kSB][kSB + 1];
+    T Ls[kSB][kSB + 1];   // off-diagonal block being applied
+    T Ld[kSB][kSB + 1];   // this CTA's diagonal block, loaded before the wait loop
+    T rinv[kSB];          // reciprocals of its diagonal
     T Xs[kSB][kRC + 1];
     int I;
 };
+
+// Load the diagonal block (rows and columns [r0, r0+64)) into Ld and the
+// reciprocals of its diagonal into rinv; ends with a barrier.
+template <typename T, class Acc>
+__device__ void load_diag(const Acc &L, int64_t n, int64_t r0, SolveSmem<T> &sm) {
+    for (int e = threadIdx.x; e < kSB * kSB; e += blockDim.x) {
+        int r, c;
+        if (Acc::kRowsFastest) { r = e % kSB; c = e / kSB; }
+        else { r = e / kSB; c = e % kSB; }
+        const int64_t i = r0 + r, j = r0 + c;
+        T v = T(0);
+        if (i < n && j < n) {
+            if (j <= i) v = L(i, j);
+        } else if (i == j) {
+            v = T(1);
+        }
+        sm.Ld[r][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kSB) sm.rinv[threadIdx.x] = T(1) / sm.Ld[threadIdx.x][threadIdx.x];
+    __syncthreads();
+}
+
+// Solve with the diagonal block in place on sm.Xs (64 rows x 16 columns):
+// L_II y = x (forward) or L_II^T y = x (backward).  Warp w owns columns 2w
+// and 2w+1; lane l owns rows l and l+32 and receives each solved entry by a
+// shuffle, so the 64 steps need no block barrier.  Ends with a barrier.
+template <typename T, bool FWD>
+__device__ void diag_solve(SolveSmem<T> &sm) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int c0 = 2 * warp, c1 = 2 * warp + 1;
+    T a0 = sm.Xs[lane][c0], a1 = sm.Xs[lane][c1], b0 = sm.Xs[lane + 32][c0], b1 = sm.Xs[lane + 32][c1];
+#pragma unroll 4
+    for (int s = 0; s < kSB; ++s) {
+        const int k = FWD ? s : kSB - 1 - s;
+        const int owner = k & 31;
+        const bool hi = k >= 32;
+        if (lane == owner) {
+            if (hi) { b0 *= sm.rinv[k]; b1 *= sm.rinv[k]; }
+            else { a0 *= sm.rinv[k]; a1 *= sm.rinv[k]; }
+        }
+        const T x0 = __shfl_sync(0xffffffffu, hi ? b0 : a0, owner);
+        const T x1 = __shfl_sync(0xffffffffu, hi ? b1 : a1, owner);
+        // FWD: rows i > k get -L(i, k) x_k; backward: rows i < k get -L(k, i) x_k
+        const int i0 = lane, i1 = lane + 32;
+        if (FWD ? i0 > k : i0 < k) {
+            const T l = FWD ? sm.Ld[i0][k] : sm.Ld[k][i0];
+            a0 = fma(-l, x0, a0);
+            a1 = fma(-l, x1, a1);
+        }
+        if (FWD ? i1 > k : i1 < k) {
+            const T l = FWD ? sm.Ld[i1][k] : sm.Ld[k][i1];
+            b0 = fma(-l, x0, b0);
+            b1 = fma(-l, x1, b1);
+        }
+    }
+    sm.Xs[lane][c0] = a0;
+    sm.Xs[lane][c1] = a1;
+    sm.Xs[lane + 32][c0] = b0;
+    sm.Xs[lane + 32][c1] = b1;
+    __syncthreads();
+}
 
 // Load the 64 x 64 block of L with rows [r0, r0+64) and columns [c0, c0+64)
 // (rows / columns beyond n read as the identity) into Ls[r][c] (transpose=false)
@@ -100,6 +166,7 @@ __global__ void __launch_bounds__(256) solve_fwd_kernel(Acc L, T *B, int64_t ldb
     const int c = threadIdx.x % kRC, rq = threadIdx.x / kRC;  // rows rq + 16 q
     int32_t *fl = flags + (size_t)y * nblk;
     const uint64_t deadline = global_ns() + timeout_ns;
+    load_diag<T>(L, n, (int64_t)I * kSB, sm);
     T acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -129,19 +196,10 @@ __global__ void __launch_bounds__(256) solve_fwd_kernel(Acc L, T *B, int64_t ldb
         __syncthreads();
     }
     // diagonal block: L_II y = acc
-    load_Lblock<T>(L, n, (int64_t)I * kSB, (int64_t)I * kSB, sm, false);
 #pragma unroll
     for (int q = 0; q < 4; ++q) sm.Xs[rq + 16 * q][c] = acc[q];
     __syncthreads();
-    for (int k = 0; k < kSB; ++k) {
-        if (threadIdx.x < kRC) sm.Xs[k][threadIdx.x] = sm.Xs[k][threadIdx.x] / sm.Ls[k][k];
-        __syncthreads();
-        for (int e = threadIdx.x; e < (kSB - 1 - k) * kRC; e += blockDim.x) {
-            const int i = k + 1 + e / kRC, cc = e % kRC;
-            sm.Xs[i][cc] = fma(-sm.Ls[i][k], sm.Xs[k][cc], sm.Xs[i][cc]);
-        }
-        __syncthreads();
-    }
+    diag_solve<T, true>(sm);
     for (int e = threadIdx.x; e < kSB * kRC; e += blockDim.x) {
         const int k = e / kRC, cc = e % kRC;
         const int64_t i = (int64_t)I * kSB + k;
@@ -170,6 +228,7 @@ __global__ void __launch_bounds__(256) solve_bwd_kernel(Acc L, T *B, int64_t ldb
     const int c = threadIdx.x % kRC, rq = threadIdx.x / kRC;
     int32_t *fl = flags + (size_t)y * nblk;
     const uint64_t deadline = global_ns() + timeout_ns;
+    load_diag<T>(L, n, (int64_t)I * kSB, sm);
     T acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -199,20 +258,11 @@ __global__ void __launch_bounds__(256) solve_bwd_kernel(Acc L, T *B, int64_t ldb
         }
         __syncthreads();
     }
-    // diagonal block: L_II^T x = acc  (Ls[r][c] = L_II(r, c), lower)
-    load_Lblock<T>(L, n, (int64_t)I * kSB, (int64_t)I * kSB, sm, false);
+    // diagonal block: L_II^T x = acc  (Ld[r][c] = L_II(r, c), lower)
 #pragma unroll
     for (int q = 0; q < 4; ++q) sm.Xs[rq + 16 * q][c] = acc[q];
     __syncthreads();
-    for (int k = kSB - 1; k >= 0; --k) {
-        if (threadIdx.x < kRC) sm.Xs[k][threadIdx.x] = sm.Xs[k][threadIdx.x] / sm.Ls[k][k];
-        __syncthreads();
-        for (int e = threadIdx.x; e < k * kRC; e += blockDim.x) {
-            const int i = e / kRC, cc = e % kRC;   // rows i < k: x_i -= L(k, i) x_k
-            sm.Xs[i][cc] = fma(-sm.Ls[k][i], sm.Xs[k][cc], sm.Xs[i][cc]);
-        }
-        __syncthreads();
-    }
+    diag_solve<T, false>(sm);
     for (int e = threadIdx.x; e < kSB * kRC; e += blockDim.x) {
         const int k = e / kRC, cc = e % kRC;
         const int64_t i = (int64_t)I * kSB + k;
