@@ -49,6 +49,7 @@ struct BatchBody {
     using Smem = BatchSmem<T>;
     static constexpr bool kSolveTask = true;
     static constexpr int kCtasPerSm = 4;
+    static constexpr int kBlock = kThreads;
     static constexpr size_t kSmemBytes = sizeof(BatchSmem<T>);
     static __device__ __forceinline__ void cta_init(const Args &, Smem &) {}
     static __device__ __forceinline__ void cta_fini(const Args &, Smem &) {}

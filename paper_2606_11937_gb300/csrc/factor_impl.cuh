@@ -10,6 +10,7 @@
 //   static __device__ void run(const Args &, const SchedArgs &, int m, int I, int K, int J, Smem &);
 //   static constexpr bool kSolveTask;  // a SOLVE task follows POTRF(M-1) of every matrix
 //   static constexpr int kCtasPerSm;   // default persistent CTAs per SM
+//   static constexpr int kBlock;       // threads per CTA (the tile routines use the first 256)
 //   static __device__ void solve(const Args &, const SchedArgs &, int m, Smem &);
 #pragma once
 
@@ -177,6 +178,7 @@ struct SimtBody {
     using Smem = SimtSmem<T>;
     static constexpr bool kSolveTask = false;
     static constexpr int kCtasPerSm = 4;  // DFMA latency is hidden by several task CTAs per SM
+    static constexpr int kBlock = kThreads;
     static constexpr size_t kSmemBytes = sizeof(SimtSmem<T>);
     static __device__ __forceinline__ void cta_init(const Args &, Smem &) {}
     static __device__ __forceinline__ void cta_fini(const Args &, Smem &) {}
@@ -220,7 +222,7 @@ template <class Body>
 constexpr size_t body_smem_bytes() { return Body::kSmemBytes + 1024; }
 
 template <class Body>
-__global__ void __launch_bounds__(256) fj_potrf_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
+__global__ void __launch_bounds__(Body::kBlock) fj_potrf_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
                                                        int J) {
     typename Body::Smem &sm = body_smem<Body>();
     if (ld_acquire_s32(&a.ctl->abort)) return;
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(256) fj_potrf_kernel(const __grid_constant__ t
 }
 
 template <class Body>
-__global__ void __launch_bounds__(256) fj_trsm_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
+__global__ void __launch_bounds__(Body::kBlock) fj_trsm_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
                                                       int J) {
     typename Body::Smem &sm = body_smem<Body>();
     if (ld_acquire_s32(&a.ctl->abort)) return;
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(256) fj_trsm_kernel(const __grid_constant__ ty
 
 // collapsed: one CTA per trailing lower tile (I, K), J < K <= I
 template <class Body>
-__global__ void __launch_bounds__(256) fj_update_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
+__global__ void __launch_bounds__(Body::kBlock) fj_update_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
                                                         int J) {
     typename Body::Smem &sm = body_smem<Body>();
     if (ld_acquire_s32(&a.ctl->abort)) return;
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(256) fj_update_kernel(const __grid_constant__ 
 
 // naive: one CTA per block row I walks K = J+1 .. I (SYRK last)
 template <class Body>
-__global__ void __launch_bounds__(256) fj_update_naive_kernel(const __grid_constant__ typename Body::Args g,
+__global__ void __launch_bounds__(Body::kBlock) fj_update_naive_kernel(const __grid_constant__ typename Body::Args g,
                                                               SchedArgs a, int J) {
     typename Body::Smem &sm = body_smem<Body>();
     if (ld_acquire_s32(&a.ctl->abort)) return;
@@ -280,15 +282,15 @@ int run_fork_join(const typename Body::Args &g, const SchedArgs &a, int M, bool 
     const size_t smem = body_smem_bytes<Body>();
     int L = 0;
     for (int J = 0; J < M; ++J) {
-        fj_potrf_kernel<Body><<<1, kThreads, smem, st>>>(g, a, J);
+        fj_potrf_kernel<Body><<<1, Body::kBlock, smem, st>>>(g, a, J);
         ++L;
         const int rest = M - J - 1;
         if (rest > 0) {
-            fj_trsm_kernel<Body><<<rest, kThreads, smem, st>>>(g, a, J);
+            fj_trsm_kernel<Body><<<rest, Body::kBlock, smem, st>>>(g, a, J);
             if (naive)
-                fj_update_naive_kernel<Body><<<rest, kThreads, smem, st>>>(g, a, J);
+                fj_update_naive_kernel<Body><<<rest, Body::kBlock, smem, st>>>(g, a, J);
             else
-                fj_update_kernel<Body><<<(unsigned)((int64_t)rest * (rest + 1) / 2), kThreads, smem, st>>>(g, a, J);
+                fj_update_kernel<Body><<<(unsigned)((int64_t)rest * (rest + 1) / 2), Body::kBlock, smem, st>>>(g, a, J);
             L += 2;
         }
     }
@@ -449,7 +451,7 @@ __device__ void df_notify(const typename Body::Args &g, const SchedArgs &a, cons
 }
 
 template <class Body>
-__global__ void __launch_bounds__(256) df_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a0,
+__global__ void __launch_bounds__(Body::kBlock) df_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a0,
                                                  DFArgs d) {
     typename Body::Smem &sm = body_smem<Body>();
     __shared__ unsigned long long s_task;
@@ -555,7 +557,7 @@ int df_grid(int num_ctas) {
     static int occ_cached = 0;
     int occ = occ_cached;
     if (occ == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, df_kernel<Body>, kThreads, body_smem_bytes<Body>()) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, df_kernel<Body>, Body::kBlock, body_smem_bytes<Body>()) !=
                 cudaSuccess ||
             occ < 1) {
             cudaGetLastError();
@@ -582,7 +584,7 @@ int launch_dataflow(const typename Body::Args &g, const SchedArgs &a, DFArgs d, 
     int rc;
     if ((rc = set_smem_attr<Body>(df_kernel<Body>))) return rc;
     if (e0) CHOL_CUDA(cudaEventRecord(e0, st));
-    df_kernel<Body><<<df_grid<Body>(o.num_ctas), kThreads, body_smem_bytes<Body>(), st>>>(g, a, d);
+    df_kernel<Body><<<df_grid<Body>(o.num_ctas), Body::kBlock, body_smem_bytes<Body>(), st>>>(g, a, d);
     *launches = 2;
     CHOL_CUDA(cudaGetLastError());
     return CHOL_OK;

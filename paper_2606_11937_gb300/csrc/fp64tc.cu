@@ -42,7 +42,7 @@ constexpr double kTrsmKappa = 65536.0;
 
 // kappa_inf(L) = max_r sum_c |L_rc| * max_c sum_r |Y_rc| for the lower
 // triangular L and Y = L^{-T} (row sums of L^{-1} are column sums of Y).
-// All threads; the result is valid in every thread.
+// Threads 0..255 (simt_sync); the result is valid in each of them.
 __device__ double oz_kappa_inf(const double *L, const double *Y, double *red) {
     double mL = 0.0, mY = 0.0;
     for (int i = threadIdx.x; i < kOzNb; i += kThreads) {
@@ -60,13 +60,13 @@ __device__ double oz_kappa_inf(const double *L, const double *Y, double *red) {
         red[threadIdx.x / 32] = mL;
         red[8 + threadIdx.x / 32] = mY;
     }
-    __syncthreads();
+    simt_sync();
     double a = 0.0, b = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) {
         a = fmax(a, red[w]);
         b = fmax(b, red[8 + w]);
     }
-    __syncthreads();
+    simt_sync();
     return a * b;
 }
 
@@ -75,6 +75,7 @@ struct OzBody {
     using Smem = OzSmem;
     static constexpr bool kSolveTask = false;
     static constexpr int kCtasPerSm = 1;
+    static constexpr int kBlock = kOzThreads;
     static constexpr size_t kSmemBytes = sizeof(OzSmem);
     static __device__ __forceinline__ void cta_init(const Args &, Smem &sm) { oz_cta_init(sm.os); }
     static __device__ __forceinline__ void cta_fini(const Args &, Smem &sm) { oz_cta_fini(sm.os); }
@@ -93,7 +94,14 @@ struct OzBody {
         if (!(a.flags & CHOL_FLAG_NOOP)) {
             switch (type) {
             case T_POTRF: {
-                const int li = tile_potrf(S.tile(J, J), kOzNb, ss);
+                // the tile routines run on threads 0..255; the others wait at the barriers
+                __shared__ int s_li, s_use_w;
+                if (threadIdx.x < kThreads) {
+                    const int li = tile_potrf(S.tile(J, J), kOzNb, ss);
+                    if (threadIdx.x == 0) s_li = li;
+                }
+                __syncthreads();
+                const int li = s_li;
                 if (li) {
                     if (threadIdx.x == 0) {
                         report_info(a.ctl, (int64_t)J * kOzNb + li);
@@ -104,12 +112,16 @@ struct OzBody {
                     // Y = I L_JJ^{-T} by the substitution kernel, then the
                     // slices of W_J = Y^T (rows of W_J are the columns of Y)
                     double *Y = g.wbuf + (size_t)J * kOzNb * kOzNb;
-                    for (int e = threadIdx.x; e < kOzNb * kOzNb; e += kThreads)
+                    for (int e = threadIdx.x; e < kOzNb * kOzNb; e += blockDim.x)
                         Y[e] = (e / kOzNb == e % kOzNb) ? 1.0 : 0.0;
                     __syncthreads();
-                    tile_trsm(Y, S.tile(J, J), kOzNb, ss, true);
-                    const double kappa = oz_kappa_inf(S.tile(J, J), Y, sm.xp[0]);
-                    const bool use_w = kappa <= kTrsmKappa;  // false also for a NaN
+                    if (threadIdx.x < kThreads) {
+                        tile_trsm(Y, S.tile(J, J), kOzNb, ss, true);
+                        const double kappa = oz_kappa_inf(S.tile(J, J), Y, sm.xp[0]);
+                        if (threadIdx.x == 0) s_use_w = kappa <= kTrsmKappa;  // false also for a NaN
+                    }
+                    __syncthreads();
+                    const bool use_w = s_use_w != 0;
                     if (use_w)
                         ozaki_split(Y, g.wslices + (size_t)J * kOzS * kOzNb * kOzNb, g.wexp + (size_t)J * kOzNb,
                                     false, true);
@@ -117,8 +129,9 @@ struct OzBody {
                 }
             } break;
             case T_TRSM: {
-                if (!__ldcg(g.wflag + J)) {  // substitution on the CUDA cores
-                    tile_trsm(S.tile(I, J), S.tile(J, J), kOzNb, ss);
+                if (!__ldcg(g.wflag + J)) {  // substitution on the CUDA cores (threads 0..255)
+                    if (threadIdx.x < kThreads) tile_trsm(S.tile(I, J), S.tile(J, J), kOzNb, ss);
+                    __syncthreads();
                     const int64_t t = tile_index(I, J);
                     ozaki_split(S.tile(I, J), g.slices + (size_t)t * kOzS * kOzNb * kOzNb, g.rexp + t * kOzNb);
                     break;
@@ -131,7 +144,7 @@ struct OzBody {
                 double *X = S.tile(I, J);
                 __nv_bfloat16 *sl = g.slices + (size_t)t * kOzS * kOzNb * kOzNb;
                 ozaki_split(X, sl, g.rexp + t * kOzNb, true, false);
-                for (int e = threadIdx.x; e < kOzNb * kOzNb; e += kThreads) X[e] = 0.0;
+                for (int e = threadIdx.x; e < kOzNb * kOzNb; e += blockDim.x) X[e] = 0.0;
                 __syncthreads();
                 const bool ok = ozaki_tile_update(sm, &g.mapA, &g.mapW, X, (int)(t * kOzS * kOzNb),
                                                   (int)((int64_t)J * kOzS * kOzNb), g.rexp + t * kOzNb,
@@ -231,7 +244,7 @@ struct OzTestArgs {
     int32_t *ok;
 };
 
-__global__ void __launch_bounds__(256) oz_test_kernel(const __grid_constant__ OzTestArgs g) {
+__global__ void __launch_bounds__(kOzThreads) oz_test_kernel(const __grid_constant__ OzTestArgs g) {
     extern __shared__ uint8_t dyn[];
     OzSmem &sm = *reinterpret_cast<OzSmem *>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023));
     oz_cta_init(sm.os);
@@ -273,7 +286,7 @@ int chol_test_ozaki_update(const double *A, const double *B, double *C) {
         g.ok = dok;
         const size_t smem = sizeof(OzSmem) + 1024;
         CHOL_CUDA(cudaFuncSetAttribute(oz_test_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        oz_test_kernel<<<1, 256, smem>>>(g);
+        oz_test_kernel<<<1, kOzThreads, smem>>>(g);
         int32_t ok = 0;
         const cudaError_t e = cudaMemcpy(&ok, dok, 4, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = cuda_fail(e, "ozaki test", __FILE__, __LINE__);

@@ -24,7 +24,11 @@
 // alternate between the two halves of the 512 columns: the epilogue of one
 // quarter runs while the tensor cores accumulate the next.  The 8 B slices of
 // a quarter's 32 rows (64 KB) are double-buffered in shared memory as well;
-// the A slices stream through a ring of stages.
+// the A slices stream through a ring of stages.  The CTA has 12 warps: TMA
+// producer (thread 0), MMA issuer (warp 1), and 8 epilogue warps, two per
+// tensor-memory lane quadrant, each converting 16 of a quarter's 32 columns
+// (two warps per SM sub-partition hide the latency of the integer and
+// binary64 epilogue arithmetic).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -37,6 +41,8 @@ namespace chol {
 constexpr int kOzNb = 128;      // tile order of the emulated path
 constexpr int kOzS = 8;         // slices per value
 constexpr int kOzStages = 4;    // A-slice ring
+constexpr int kOzThreads = 384; // 12 warps: producer, MMA issuer, 2 idle, 8 epilogue
+constexpr int kOzEpiWarps = 8;
 constexpr int kOzQ = 32;        // output columns per quarter (B rows per slice and quarter)
 constexpr int kOzABytes = 128 * 128;  // one A slice, one K-chunk of 64 (bf16): 128 rows x 128 B
 constexpr int kOzBBytes = kOzQ * 128; // one B slice, one K-chunk, one quarter's 32 rows
@@ -55,7 +61,7 @@ struct OzSmem {
     uint8_t B[2][2 * kOzS][kOzBBytes];     // 128 KB: buffer b, K-chunk kc, slice t at [b][kc * 8 + t] (the
                                            // 8 slices of a K-chunk form one 256-row K-major operand)
     uint8_t A[kOzStages][kOzABytes];       // 64 KB
-    double xp[4][32 * 32];                 // 32 KB: per epilogue warp, a 32 x 32 block of C
+    double xp[kOzEpiWarps][32 * 16];       // 32 KB: per epilogue warp, a 32 x 16 block of C
     int32_t ex[2][kOzNb];                  // row exponents of A and B
     OzShared os;
 };
@@ -82,12 +88,13 @@ __device__ __forceinline__ uint16_t small_int_bf16(uint32_t a, uint32_t neg) {
 // [56 - 7s, 63 - 7s) of X -- the digits the recursion t = 128 x,
 // a = trunc(t), x = t - a produces -- computed with integer operations on
 // the binary64 encoding.  Element (r, c) is T[r * 128 + c], or T[c * 128 + r]
-// with `transpose`; `negate` splits -T.  All 256 threads; ends with a barrier.
+// with `transpose`; `negate` splits -T.  All threads of the CTA; ends with a
+// barrier.
 __device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32_t *rexp, bool negate = false,
                                    bool transpose = false) {
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
     uint16_t *out = reinterpret_cast<uint16_t *>(slices);
-    for (int r = warp; r < kOzNb; r += 8) {
+    for (int r = warp; r < kOzNb; r += nwarps) {
         double v[4];
         double m = 0.0;
 #pragma unroll
@@ -158,9 +165,9 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
-// index of element (r, j) of a warp's 32 x 32 double block in shared memory,
+// index of element (r, j) of a warp's 32 x 16 double block in shared memory,
 // 16-byte segments XOR-swizzled by row so row- and column-wise accesses spread
-__device__ __forceinline__ int xp_idx(int r, int j) { return r * 32 + ((((j >> 1) ^ (r & 15)) << 1) | (j & 1)); }
+__device__ __forceinline__ int xp_idx(int r, int j) { return r * 16 + ((((j >> 1) ^ (r & 7)) << 1) | (j & 1)); }
 
 inline __device__ void oz_cta_init(OzShared &os) {
     if (threadIdx.x == 0) {
@@ -172,7 +179,7 @@ inline __device__ void oz_cta_init(OzShared &os) {
             mbar_init(&os.bfull[b], 1);
             mbar_init(&os.bfree[b], 1);
             mbar_init(&os.acc_full[b], 1);
-            mbar_init(&os.tmem_empty[b], 4);
+            mbar_init(&os.tmem_empty[b], kOzEpiWarps);
         }
         mbar_init(&os.drain, 1);
         os.ring = 0;
@@ -204,8 +211,8 @@ inline __device__ void oz_cta_fini(OzShared &os) {
 // C (row-major 128 x 128 binary64) -= A B^T where A, B are given by their
 // slices: rows [aRow0, aRow0 + 8*128) and [bRow0, ...) of the slice maps
 // (slice s of a tile at rows base + 128 s) and their row exponents.  mapA has
-// 128-row boxes, mapB 32-row boxes.  Called by all 256 threads; false if a
-// bounded wait expired.
+// 128-row boxes, mapB 32-row boxes.  Called by all kOzThreads threads; false
+// if a bounded wait expired.
 //
 // Quarter u (counted across tasks) uses B buffer and tensor-memory half
 // b = u & 1; the k-th use of a buffer waits on its barriers with parity k & 1.
@@ -304,35 +311,45 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
         // ---------------- epilogue: 8 exact FP32 group sums -> binary64
         // G_g (d = g + 2) are integers below 2^24.  hi = sum_{g<4} G_g 2^{7(3-g)}
         // and lo = sum_{g>=4} G_g 2^{7(7-g)} are exact int64 (< 2^46); the
-        // update is A B^T = 2^{e_r + e_c} (hi 2^-35 + lo 2^-63).  Each warp owns
-        // 32 rows; per quarter it stages its 32 x 32 block of C in shared memory
+        // update is A B^T = 2^{e_r + e_c} (hi 2^-35 + lo 2^-63).  Warp w owns
+        // the 32 rows of lane quadrant w % 4 and columns 16 ((w - 4) / 4) ..
+        // +15 of each quarter; it stages its 32 x 16 block of C in shared memory
         // with coalesced asynchronous copies, each lane (one row) applies its
         // row's update there, and the block is written back coalesced.
-        const int q = warp - 4;
+        const int ew = warp - 4;
+        const int q = warp & 3;
+        const int ch = ew >> 2;
         const int row = q * 32 + lane;
         // pull this row of C into L2 while the MMAs run (8 lines of 128 bytes)
+        if (ch == 0) {
 #pragma unroll
-        for (int l = 0; l < 8; ++l)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (size_t)row * kOzNb + l * 16));
-        for (int i = threadIdx.x - 128; i < kOzNb; i += 128) {
+            for (int l = 0; l < 8; ++l)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (size_t)row * kOzNb + l * 16));
+        }
+        for (int i = threadIdx.x - 128; i < kOzNb; i += 32 * kOzEpiWarps) {
             sm.ex[0][i] = __ldcg(expA + i);
             sm.ex[1][i] = __ldcg(expB + i);
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");  // the 4 epilogue warps only
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps only
         const int ea = sm.ex[0][row];
-        double *xp = sm.xp[q];
+        double *xp = sm.xp[ew];
 #pragma unroll 1
         for (int qq = 0; qq < kQuarters; ++qq) {
             const uint32_t u = q0 + qq, b = u & 1;
-            // stage this warp's 32 x 32 block of C in shared memory (async,
+            const int col0 = qq * kOzQ + ch * 16;  // first tile column of this warp's block
+            // stage this warp's 32 x 16 block of C in shared memory (async,
             // coalesced 16-byte copies) while the accumulators are produced
-            double *cblk = C + (size_t)(q * 32) * kOzNb + qq * kOzQ;
+            double *cblk = C + (size_t)(q * 32) * kOzNb + col0;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int idx = i * 32 + lane, rr = idx >> 4, seg = idx & 15;
+            for (int i = 0; i < 8; ++i) {
+                const int idx = i * 32 + lane, rr = idx >> 3, seg = idx & 7;
                 cp_async16(smem_u32(xp + xp_idx(rr, 2 * seg)), cblk + (size_t)rr * kOzNb + 2 * seg);
             }
-            if (!mbar_wait(&os.acc_full[b], (u >> 1) & 1, deadline)) {
+            // one lane polls, the others wait at the shuffle
+            bool got = true;
+            if (lane == 0) got = mbar_wait(&os.acc_full[b], (u >> 1) & 1, deadline);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) {
                 oz_fail(os);
                 cp_async_wait_all();
                 break;
@@ -341,29 +358,25 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
             // group d = g + 2 holds at most d - 1 products below 2^21 each, so
             // G_{2k} 128 + G_{2k+1} fits in int32; hi = (t01 << 14) + t23 and
             // lo = (t45 << 14) + t67 are exact int64.
-            long long hi[32], lo[32];
-            const uint32_t tb = os.tmem_base + ((uint32_t)(q * 32) << 16) + b * (uint32_t)(kOzS * kOzQ);
+            long long hi[16], lo[16];
+            const uint32_t tb =
+                os.tmem_base + ((uint32_t)(q * 32) << 16) + b * (uint32_t)(kOzS * kOzQ) + (uint32_t)(ch * 16);
 #pragma unroll
             for (int half4 = 0; half4 < 2; ++half4) {
-                int32_t t0[32], t1[32];
+                uint32_t r0[16], r1[16], r2[16], r3[16];
+                const int g = half4 * 4;
+                tmem_ld16(tb + (uint32_t)(g * kOzQ), r0);
+                tmem_ld16(tb + (uint32_t)((g + 1) * kOzQ), r1);
+                tmem_ld16(tb + (uint32_t)((g + 2) * kOzQ), r2);
+                tmem_ld16(tb + (uint32_t)((g + 3) * kOzQ), r3);
+                tmem_ld_wait();
 #pragma unroll
-                for (int pr = 0; pr < 2; ++pr) {
-                    const int g = half4 * 4 + pr * 2;
-                    uint32_t ra[32], rb[32];
-                    tmem_ld32(tb + (uint32_t)(g * kOzQ), ra);
-                    tmem_ld32(tb + (uint32_t)((g + 1) * kOzQ), rb);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int32_t v = __float2int_rn(__uint_as_float(ra[j])) * 128 +
-                                          __float2int_rn(__uint_as_float(rb[j]));
-                        if (pr == 0) t0[j] = v;
-                        else t1[j] = v;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const long long w = ((long long)t0[j] << 14) + (long long)t1[j];
+                for (int j = 0; j < 16; ++j) {
+                    const int32_t t01 = __float2int_rn(__uint_as_float(r0[j])) * 128 +
+                                        __float2int_rn(__uint_as_float(r1[j]));
+                    const int32_t t23 = __float2int_rn(__uint_as_float(r2[j])) * 128 +
+                                        __float2int_rn(__uint_as_float(r3[j]));
+                    const long long w = ((long long)t01 << 14) + (long long)t23;
                     if (half4 == 0) hi[j] = w;
                     else lo[j] = w;
                 }
@@ -377,8 +390,8 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
             // (|hi|, |lo| < 2^47) unless a row or column scale is extreme
             bool ok_range = true;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int eab = ea + sm.ex[1][qq * kOzQ + j];
+            for (int j = 0; j < 16; ++j) {
+                const int eab = ea + sm.ex[1][col0 + j];
                 ok_range &= (eab >= -900 && eab <= 900);
             }
             cp_async_wait_all();
@@ -386,23 +399,23 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
             // this lane's row of the block: C <- (C - hi 2^(eab-35)) - lo 2^(eab-63)
             if (__all_sync(0xffffffffu, ok_range)) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int eab = ea + sm.ex[1][qq * kOzQ + j];
+                for (int j = 0; j < 16; ++j) {
+                    const int eab = ea + sm.ex[1][col0 + j];
                     double &cv = xp[xp_idx(lane, j)];
                     cv = (cv - int_scaled_fast(hi[j], eab - 35)) - int_scaled_fast(lo[j], eab - 63);
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int eab = ea + sm.ex[1][qq * kOzQ + j];
+                for (int j = 0; j < 16; ++j) {
+                    const int eab = ea + sm.ex[1][col0 + j];
                     double &cv = xp[xp_idx(lane, j)];
                     cv = (cv - int_scaled(hi[j], eab - 35)) - int_scaled(lo[j], eab - 63);
                 }
             }
             __syncwarp();
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int idx = i * 32 + lane, rr = idx >> 4, seg = idx & 15;
+            for (int i = 0; i < 8; ++i) {
+                const int idx = i * 32 + lane, rr = idx >> 3, seg = idx & 7;
                 const double2 v = *reinterpret_cast<const double2 *>(xp + xp_idx(rr, 2 * seg));
                 *reinterpret_cast<double2 *>(cblk + (size_t)rr * kOzNb + 2 * seg) = v;
             }

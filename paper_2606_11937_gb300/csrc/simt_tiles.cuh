@@ -2,7 +2,8 @@
 // (DFMA for binary64, FFMA for binary32), for 256-thread CTAs.
 //
 // Tiles are nb x nb, row-major (element (r, c) at r * ld + c).  Every routine
-// is executed by all 256 threads of the CTA and ends with a __syncthreads().
+// is executed by the first 256 threads of the CTA (all of it for 256-thread
+// bodies) and ends with a barrier among them (named barrier 2, simt_sync).
 //   tile_potrf : A_JJ <- chol(A_JJ)                   (lower; returns local info)
 //   tile_trsm  : A_IJ <- A_IJ A_JJ^{-T}
 //   tile_syrk  : A_II <- A_II - A_IJ A_IJ^T           (lower triangle only)
@@ -19,6 +20,10 @@
 namespace chol {
 
 constexpr int kThreads = 256;
+
+// Barrier among threads 0..255: the tile routines below synchronise with it,
+// so a body with more threads runs them on its first 256 threads only.
+__device__ __forceinline__ void simt_sync() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
 constexpr int kBlk = 64;   // output block edge of block_nt_update
 constexpr int kBK = 16;    // k-chunk staged per iteration
 constexpr int kIB = 32;    // panel width of the blocked POTRF / TRSM
@@ -65,7 +70,7 @@ __device__ void block_nt_update(T *C, int ldc, const T *A, int lda, const T *B, 
             sm.As[kk][r] = (r < m && kk < kc) ? ldg_cg(A + (size_t)r * lda + k0 + kk) : T(0);
             sm.Bs[kk][r] = (r < n && kk < kc) ? ldg_cg(B + (size_t)r * ldb + k0 + kk) : T(0);
         }
-        __syncthreads();
+        simt_sync();
 #pragma unroll
         for (int kk = 0; kk < kBK; ++kk) {
             T a[MI], b[MI];
@@ -78,7 +83,7 @@ __device__ void block_nt_update(T *C, int ldc, const T *A, int lda, const T *B, 
 #pragma unroll
                 for (int j = 0; j < MI; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
-        __syncthreads();
+        simt_sync();
     }
 #pragma unroll
     for (int i = 0; i < MI; ++i)
@@ -90,7 +95,7 @@ __device__ void block_nt_update(T *C, int ldc, const T *A, int lda, const T *B, 
                 *p = ldg_cg(p) - acc[i][j];
             }
         }
-    __syncthreads();
+    simt_sync();
 }
 
 // Subtract A B^T from the block region C[0:m, 0:n] (any m, n) by 64 x 64 (or
@@ -139,9 +144,9 @@ __device__ void stage_diag(const T *L, int ld, int jb, int w, SimtSmem<T> &sm) {
         }
         sm.D[r][c] = v;
     }
-    __syncthreads();
+    simt_sync();
     if (threadIdx.x < kIB) sm.Dinv[threadIdx.x] = T(1) / sm.D[threadIdx.x][threadIdx.x];
-    __syncthreads();
+    simt_sync();
 }
 
 // Rows [r0, r1) of P (columns jb .. jb+w) <- P * D^{-T}: each thread runs the
@@ -164,7 +169,7 @@ __device__ void rows_trsm(T *P, int ld, int jb, int w, int r0, int r1, SimtSmem<
         for (int j = 0; j < kIB; ++j)
             if (j < w) row[j] = x[j];
     }
-    __syncthreads();
+    simt_sync();
 }
 
 // A_IJ <- A_IJ L^{-T}: blocked right-looking over panels of kIB columns.
@@ -206,7 +211,7 @@ __device__ int tile_potrf(T *A, int nb, SimtSmem<T> &sm) {
             sm.D[r][c] = v;
         }
         if (threadIdx.x == 0) sm.flag = 0;
-        __syncthreads();
+        simt_sync();
         if (threadIdx.x < 32) {
             const int lane = threadIdx.x;
             int fail = 0;
@@ -229,10 +234,10 @@ __device__ int tile_potrf(T *A, int nb, SimtSmem<T> &sm) {
             }
             if (lane == 0) sm.flag = fail;
         }
-        __syncthreads();
+        simt_sync();
         if (sm.flag) {
             const int f = sm.flag;
-            __syncthreads();
+            simt_sync();
             return jb + f;
         }
         // write back the factored block, reciprocals of its diagonal
@@ -241,7 +246,7 @@ __device__ int tile_potrf(T *A, int nb, SimtSmem<T> &sm) {
             if (c <= r) A[(size_t)(jb + r) * nb + jb + c] = sm.D[r][c];
         }
         if (threadIdx.x < kIB) sm.Dinv[threadIdx.x] = T(1) / sm.D[threadIdx.x][threadIdx.x];
-        __syncthreads();
+        simt_sync();
         const int r0 = jb + w;
         if (r0 < nb) {
             rows_trsm(A, nb, jb, w, r0, nb, sm);
