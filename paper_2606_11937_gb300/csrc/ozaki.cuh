@@ -40,11 +40,12 @@ namespace chol {
 
 constexpr int kOzNb = 128;      // tile order of the emulated path
 constexpr int kOzS = 8;         // slices per value
-constexpr int kOzStages = 4;    // A-slice ring
+constexpr int kOzStages = 2;    // A-slice ring (one stage = one slice, both K-chunks)
 constexpr int kOzThreads = 384; // 12 warps: producer, MMA issuer, 2 idle, 8 epilogue
 constexpr int kOzEpiWarps = 8;
 constexpr int kOzQ = 32;        // output columns per quarter (B rows per slice and quarter)
-constexpr int kOzABytes = 128 * 128;  // one A slice, one K-chunk of 64 (bf16): 128 rows x 128 B
+constexpr int kOzAChunk = 128 * 128;  // one A slice, one K-chunk of 64 (bf16): 128 rows x 128 B
+constexpr int kOzABytes = 2 * kOzAChunk;  // one ring stage: a whole A slice
 constexpr int kOzBBytes = kOzQ * 128; // one B slice, one K-chunk, one quarter's 32 rows
 
 struct OzShared {
@@ -247,17 +248,16 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
                 for (int kc = 0; kc < 2; ++kc)
                     tma_load_2d(smem_u32(sm.B[b][kc * kOzS + t]), mapB, &os.bfull[b], kc * 64,
                                 bRow0 + t * 128 + qq * kOzQ);
-            for (int s = 0; s < kOzS && !oz_failed(os); ++s)
-                for (int kc = 0; kc < 2; ++kc, ++f) {
-                    const int st = (int)(f % kOzStages);
-                    if (f >= (uint32_t)kOzStages &&
-                        !mbar_wait(&os.empty[st], ((f / kOzStages) & 1) ^ 1, deadline)) {
-                        oz_fail(os);
-                        break;
-                    }
-                    mbar_arrive_expect_tx(&os.full[st], kOzABytes);
-                    tma_load_2d(smem_u32(sm.A[st]), mapA, &os.full[st], kc * 64, aRow0 + s * 128);
+            for (int s = 0; s < kOzS && !oz_failed(os); ++s, ++f) {
+                const int st = (int)(f % kOzStages);
+                if (f >= (uint32_t)kOzStages && !mbar_wait(&os.empty[st], ((f / kOzStages) & 1) ^ 1, deadline)) {
+                    oz_fail(os);
+                    break;
                 }
+                mbar_arrive_expect_tx(&os.full[st], kOzABytes);
+                for (int kc = 0; kc < 2; ++kc)
+                    tma_load_2d(smem_u32(sm.A[st]) + kc * kOzAChunk, mapA, &os.full[st], kc * 64, aRow0 + s * 128);
+            }
         }
         producer_idle();
     } else if (warp == 1 && lane == 0) {
@@ -287,23 +287,25 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
             tc_fence_after();
             const uint64_t bdesc[2] = {sdesc_sw128(smem_u32(sm.B[b][0])), sdesc_sw128(smem_u32(sm.B[b][kOzS]))};
             const uint32_t dbase = os.tmem_base + b * (uint32_t)(kOzS * kOzQ);
-            for (int s = 0; s < kOzS && !oz_failed(os); ++s)
-                for (int kc = 0; kc < 2; ++kc, ++f) {
-                    const int st = (int)(f % kOzStages);
-                    if (!mbar_wait(&os.full[st], (f / kOzStages) & 1, deadline)) {
-                        oz_fail(os);
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint64_t adesc = sdesc_sw128(smem_u32(sm.A[st]));
-                    const uint32_t idesc = kIdescN[kOzS - s];
-                    const uint32_t d = dbase + (uint32_t)(s * kOzQ);
+            for (int s = 0; s < kOzS && !oz_failed(os); ++s, ++f) {
+                const int st = (int)(f % kOzStages);
+                if (!mbar_wait(&os.full[st], (f / kOzStages) & 1, deadline)) {
+                    oz_fail(os);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t idesc = kIdescN[kOzS - s];
+                const uint32_t d = dbase + (uint32_t)(s * kOzQ);
+#pragma unroll
+                for (int kc = 0; kc < 2; ++kc) {
+                    const uint64_t adesc = sdesc_sw128(smem_u32(sm.A[st]) + kc * kOzAChunk);
 #pragma unroll
                     for (int k4 = 0; k4 < 4; ++k4)
                         tc_mma<false>(d, adesc + 2 * k4, bdesc[kc] + 2 * k4, idesc,
                                       (s == 0 && kc == 0 && k4 == 0) ? 0u : 1u);
-                    tc_commit(&os.empty[st]);
                 }
+                tc_commit(&os.empty[st]);
+            }
             tc_commit(&os.acc_full[b]);
             tc_commit(&os.bfree[b]);
         }
@@ -426,7 +428,7 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
     const bool ok = !oz_failed(os);
     __syncthreads();
     if (threadIdx.x == 0 && ok) {
-        os.ring = ring0 + kQuarters * kOzS * 2;
+        os.ring = ring0 + kQuarters * kOzS;
         os.quarters = q0 + kQuarters;
     }
     __syncthreads();
