@@ -50,6 +50,7 @@ struct BatchBody {
     static constexpr bool kSolveTask = true;
     static constexpr int kCtasPerSm = 4;
     static constexpr int kBlock = kThreads;
+    static constexpr bool kLag = false;
     static constexpr size_t kSmemBytes = sizeof(BatchSmem<T>);
     static __device__ __forceinline__ void cta_init(const Args &, Smem &) {}
     static __device__ __forceinline__ void cta_fini(const Args &, Smem &) {}

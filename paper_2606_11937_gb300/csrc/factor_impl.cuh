@@ -11,6 +11,10 @@
 //   static constexpr bool kSolveTask;  // a SOLVE task follows POTRF(M-1) of every matrix
 //   static constexpr int kCtasPerSm;   // default persistent CTAs per SM
 //   static constexpr int kBlock;       // threads per CTA (the tile routines use the first 256)
+//   static constexpr bool kLag;        // a task may complete after run() returns: then
+//     static bool lagging(Smem &);     //   true while the last run's completion is deferred,
+//     static bool absorbs(g, I, K, J); //   whether task (I,K,J) can start with it deferred,
+//     static void flush(g, a, Smem &); //   complete it now (all threads; df_complete_lagged)
 //   static __device__ void solve(const Args &, const SchedArgs &, int m, Smem &);
 #pragma once
 
@@ -56,6 +60,7 @@ struct DFLocal {
     DFArgs d;
     unsigned long long tk[2];  // claimed slots (priority, normal), or kNoTicket
     uint64_t next;             // a ready task held for the next iteration, or kEmptySlot
+    uint64_t lagcont;          // ready chain successor released by a deferred completion, or kEmptySlot
 };
 
 constexpr int kSolveJ = 0xFFFF;  // J marker of the fused SOLVE task (batched)
@@ -179,6 +184,7 @@ struct SimtBody {
     static constexpr bool kSolveTask = false;
     static constexpr int kCtasPerSm = 4;  // DFMA latency is hidden by several task CTAs per SM
     static constexpr int kBlock = kThreads;
+    static constexpr bool kLag = false;
     static constexpr size_t kSmemBytes = sizeof(SimtSmem<T>);
     static __device__ __forceinline__ void cta_init(const Args &, Smem &) {}
     static __device__ __forceinline__ void cta_fini(const Args &, Smem &) {}
@@ -418,6 +424,25 @@ __device__ __forceinline__ uint64_t df_release_chain(const typename Body::Args &
     return old + 1 == task_needs(I, K, J) ? pack_task(m, I, K, J) : kEmptySlot;
 }
 
+// Completion of a task whose epilogue finished after its run() returned (one
+// thread, after a barrier that orders the task's tile writes): bookkeeping,
+// release of its tile-chain successor (held in lagcont for the CTA, or queued
+// when a successor is already held), and the completed count.
+template <class Body>
+__device__ void df_complete_lagged(const typename Body::Args &g, const SchedArgs &a, int m, int I, int K, int J,
+                                   uint64_t t0) {
+    DFLocal &L = *a.dfl;
+    task_done_bookkeeping(a, task_type(I, K, J), m, I, K, J, t0);
+    if (!ld_relaxed_s32(&a.ctl->abort) && J < K) {
+        const uint64_t c = df_release_chain<Body>(g, a, L.d, m, Body::tiles(g, m), I, K, J + 1);
+        if (c != kEmptySlot) {
+            if (L.lagcont == kEmptySlot) L.lagcont = c;
+            else df_push(a.ctl, L.d, df_is_priority(a.flags, I, K, J + 1) ? 0 : 1, c);
+        }
+    }
+    atomicAdd(&a.ctl->completed, 1ull);
+}
+
 template <class Body>
 __device__ __forceinline__ void df_notify_one(const typename Body::Args &g, const SchedArgs &a, const DFArgs &d,
                                               int m, int M, int I, int K, int J) {
@@ -464,56 +489,93 @@ __global__ void __launch_bounds__(Body::kBlock) df_kernel(const __grid_constant_
         s_local.d = d;
         s_local.tk[0] = s_local.tk[1] = kNoTicket;
         s_local.next = kEmptySlot;
+        s_local.lagcont = kEmptySlot;
     }
     Body::cta_init(g, sm);
     uint64_t cont = kEmptySlot;  // thread 0: ready chain successor of the last task
     int32_t aborted = 0;         // thread 0: abort flag seen after the last task
+    __shared__ int s_flush;
     for (;;) {
         if (threadIdx.x == 0) {
             uint64_t v = 0;
             int cmd = 0;
             DFLocal &L = s_local;
+            bool lag = false;
+            if constexpr (Body::kLag) lag = Body::lagging(sm);
             if (aborted) {
                 cmd = -1;
-            } else if (L.next != kEmptySlot || cont != kEmptySlot) {
-                // a task held from a take-ahead and/or the chain successor: run a
-                // priority-class one first, else the chain successor (its tile is
-                // hot in L2), and hold the other for the next iteration
-                uint64_t pick = cont, keep = L.next;
-                if (pick == kEmptySlot || (keep != kEmptySlot && df_is_priority(a.flags, (int)((keep >> 32) & 0xffff),
-                                                                              (int)((keep >> 16) & 0xffff),
-                                                                              (int)(keep & 0xffff)) &&
-                                           !df_is_priority(a.flags, (int)((pick >> 32) & 0xffff),
-                                                           (int)((pick >> 16) & 0xffff), (int)(pick & 0xffff)))) {
-                    pick = L.next;
-                    keep = cont;
-                }
-                L.next = keep;
+            } else {
+                // candidates: the chain successor of the last task (cont), one
+                // released by a deferred completion (lagcont), a task taken ahead
+                // (next).  Run a priority-class one first, else a chain successor
+                // (its tile is hot in L2); hold one other, queue a third.
+                uint64_t c[3] = {cont, L.lagcont, L.next};
                 cont = kEmptySlot;
-                cmd = 1;
-                v = pick;
-                // a normal-class chain successor, nothing held, priority work
-                // waiting: the successor goes to the normal queue
-                if (keep == kEmptySlot && (a.flags & CHOL_FLAG_PRIORITY) &&
-                    !df_is_priority(a.flags, (int)((pick >> 32) & 0xffff), (int)((pick >> 16) & 0xffff),
-                                    (int)(pick & 0xffff))) {
-                    const unsigned long long h = ld_relaxed_u64(&ctl->head[0]);
-                    const unsigned long long t = ld_relaxed_u64(&ctl->tail[0]);
-                    if (h < t) {
-                        df_push(ctl, d, 1, pick);
-                        cmd = 0;
+                L.lagcont = kEmptySlot;
+                L.next = kEmptySlot;
+                int pick = -1;
+                for (int i = 0; i < 3 && pick < 0; ++i)
+                    if (c[i] != kEmptySlot && df_is_priority(a.flags, (int)((c[i] >> 32) & 0xffff),
+                                                              (int)((c[i] >> 16) & 0xffff), (int)(c[i] & 0xffff)))
+                        pick = i;
+                for (int i = 0; i < 3 && pick < 0; ++i)
+                    if (c[i] != kEmptySlot) pick = i;
+                int held = 0;
+                for (int i = 0; i < 3; ++i) {
+                    if (i == pick || c[i] == kEmptySlot) continue;
+                    if (!held++) L.next = c[i];
+                    else df_push(ctl, d, df_is_priority(a.flags, (int)((c[i] >> 32) & 0xffff),
+                                                        (int)((c[i] >> 16) & 0xffff), (int)(c[i] & 0xffff)) ? 0 : 1,
+                                 c[i]);
+                }
+                if (pick >= 0) {
+                    cmd = 1;
+                    v = c[pick];
+                    // a normal-class successor, nothing held, priority work
+                    // waiting: it goes to the normal queue
+                    if (!held && (a.flags & CHOL_FLAG_PRIORITY) &&
+                        !df_is_priority(a.flags, (int)((v >> 32) & 0xffff), (int)((v >> 16) & 0xffff),
+                                        (int)(v & 0xffff))) {
+                        const unsigned long long h = ld_relaxed_u64(&ctl->head[0]);
+                        const unsigned long long t = ld_relaxed_u64(&ctl->tail[0]);
+                        if (h < t) {
+                            df_push(ctl, d, 1, v);
+                            cmd = 0;
+                        }
+                    }
+                }
+                if (cmd == 0) {
+                    if (lag) {
+                        // a deferred completion may release what we would wait
+                        // for: only a non-blocking attempt, else complete it first
+                        cmd = df_try_pop(ctl, L, &v) ? 1 : 2;
+                    } else {
+                        cmd = df_pop(ctl, d, &v, L.tk);
                     }
                 }
             }
-            if (cmd == 0) cmd = df_pop(ctl, d, &v, L.tk);
+            int fl = 0;
+            if constexpr (Body::kLag) {
+                if (lag && cmd == 1)
+                    fl = !Body::absorbs(g, (int)((v >> 32) & 0xffff), (int)((v >> 16) & 0xffff), (int)(v & 0xffff));
+                if (lag && cmd < 0) fl = 1;
+            }
             if (cmd == 1) fence_acq_rel();
             s_task = v;
             s_cmd = cmd;
+            s_flush = fl;
         }
         __syncthreads();
         const int cmd = s_cmd;
         const uint64_t v = s_task;
+        const int fl = s_flush;
         __syncthreads();
+        if constexpr (Body::kLag) {
+            if (cmd == 2 || fl) {
+                Body::flush(g, a, sm);  // all threads
+                if (cmd == 2) continue;
+            }
+        }
         if (cmd != 1) break;
         const int J = (int)(v & 0xffff), K = (int)((v >> 16) & 0xffff), I = (int)((v >> 32) & 0xffff);
         const int m = (int)(v >> 48);
@@ -522,7 +584,9 @@ __global__ void __launch_bounds__(Body::kBlock) df_kernel(const __grid_constant_
         } else {
             Body::run(g, a, m, I, K, J, sm);   // ends with __syncthreads()
         }
-        if (threadIdx.x < 32) {
+        bool lagged = false;
+        if constexpr (Body::kLag) lagged = Body::lagging(sm);
+        if (threadIdx.x < 32 && !lagged) {
             // No separate fence: every way a successor is published is a
             // release at GPU scope (the acq_rel counter update, the release
             // store of a queue slot) by a warp-0 thread that passed the
@@ -536,6 +600,8 @@ __global__ void __launch_bounds__(Body::kBlock) df_kernel(const __grid_constant_
                 atomicAdd(&ctl->completed, 1ull);
                 aborted = ab;
             }
+        } else if (threadIdx.x == 0 && lagged) {
+            aborted = ld_relaxed_s32(&ctl->abort);
         }
     }
     Body::cta_fini(g, sm);

@@ -77,6 +77,34 @@ struct OzBody {
     static constexpr int kCtasPerSm = 1;
     static constexpr int kBlock = kOzThreads;
     static constexpr size_t kSmemBytes = sizeof(OzSmem);
+    // In the dataflow kernel a SYRK/GEMM leaves the epilogue of its last
+    // quarter to the next tile update on this CTA (which applies it while its
+    // own first quarter is on the tensor cores) or to flush(); the task
+    // completes (successors released) when that quarter is stored.
+    static constexpr bool kLag = true;
+    static __device__ __forceinline__ bool lagging(Smem &sm) { return sm.os.pend != 0; }
+    static __device__ __forceinline__ bool absorbs(const Args &g, int I, int K, int J) {
+        const int type = task_type(I, K, J);
+        if (type == T_POTRF) return false;
+        if (type == T_TRSM) return __ldcg(g.wflag + J) != 0;  // the emulated TRSM is a tile update
+        return true;
+    }
+    static __device__ void flush(const Args &g, const SchedArgs &a, Smem &sm) {
+        const bool ok = ozaki_flush(sm, g.timeout_ns, Done{g, a});
+        if (!ok && threadIdx.x == 0) {
+            if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 4;
+            st_release_s32(&a.ctl->abort, 1);
+        }
+    }
+    // completion of a deferred update (one epilogue thread)
+    struct Done {
+        const Args &g;
+        const SchedArgs &a;
+        __device__ void operator()(uint64_t w, uint64_t t0) const {
+            df_complete_lagged<OzBody>(g, a, (int)(w >> 48), (int)((w >> 32) & 0xffff), (int)((w >> 16) & 0xffff),
+                                       (int)(w & 0xffff), t0);
+        }
+    };
     static __device__ __forceinline__ void cta_init(const Args &, Smem &sm) { oz_cta_init(sm.os); }
     static __device__ __forceinline__ void cta_fini(const Args &, Smem &sm) { oz_cta_fini(sm.os); }
     static __device__ __forceinline__ int tiles(const Args &g, int) { return g.S.M; }
@@ -148,7 +176,7 @@ struct OzBody {
                 __syncthreads();
                 const bool ok = ozaki_tile_update(sm, &g.mapA, &g.mapW, X, (int)(t * kOzS * kOzNb),
                                                   (int)((int64_t)J * kOzS * kOzNb), g.rexp + t * kOzNb,
-                                                  g.wexp + (size_t)J * kOzNb, g.timeout_ns, take_ahead);
+                                                  g.wexp + (size_t)J * kOzNb, g.timeout_ns, take_ahead, Done{g, a});
                 if (ok) {
                     ozaki_split(X, sl, g.rexp + t * kOzNb);
                 } else if (threadIdx.x == 0) {
@@ -160,7 +188,8 @@ struct OzBody {
                 const int64_t ta = tile_index(I, J), tb = tile_index(K, J);
                 const bool ok = ozaki_tile_update(sm, &g.mapA, &g.mapB, S.tile(I, K), (int)(ta * kOzS * kOzNb),
                                                   (int)(tb * kOzS * kOzNb), g.rexp + ta * kOzNb,
-                                                  g.rexp + tb * kOzNb, g.timeout_ns, take_ahead);
+                                                  g.rexp + tb * kOzNb, g.timeout_ns, take_ahead, Done{g, a},
+                                                  a.dfl != nullptr, pack_task(m, I, K, J), t0);
                 if (!ok && threadIdx.x == 0) {
                     if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 4;
                     st_release_s32(&a.ctl->abort, 1);
@@ -169,7 +198,7 @@ struct OzBody {
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) task_done_bookkeeping(a, type, m, I, K, J, t0);
+        if (threadIdx.x == 0 && !sm.os.pend) task_done_bookkeeping(a, type, m, I, K, J, t0);
     }
     static __device__ void solve(const Args &, const SchedArgs &, int, Smem &) {}
 };

@@ -165,6 +165,7 @@ struct MixedBody {
     static constexpr bool kSolveTask = false;
     static constexpr int kCtasPerSm = 1;  // one CTA owns the SM's shared memory and tensor memory
     static constexpr int kBlock = kThreads;
+    static constexpr bool kLag = false;
     static constexpr size_t kSmemBytes = sizeof(MixedSmem);
     static __device__ __forceinline__ void cta_init(const Args &, Smem &sm) { tc_cta_init(sm.ts); }
     static __device__ __forceinline__ void cta_fini(const Args &, Smem &sm) { tc_cta_fini(sm.ts); }

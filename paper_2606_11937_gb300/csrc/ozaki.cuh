@@ -56,6 +56,14 @@ struct OzShared {
     uint32_t ring;      // A-stage fills before the current task
     uint32_t quarters;  // quarters (B loads / accumulations) before the current task
     int32_t fail;
+    // the last quarter of an update whose epilogue was deferred to the next
+    // call (ozaki_tile_update with defer_last) or to ozaki_flush
+    int32_t pend;
+    uint32_t pend_u;             // its quarter index
+    double *pend_C;
+    const int32_t *pend_expA, *pend_expB;
+    uint64_t pend_task;          // opaque word handed to the completion callback
+    uint64_t pend_t0;
 };
 
 struct OzSmem {
@@ -63,7 +71,7 @@ struct OzSmem {
                                            // 8 slices of a K-chunk form one 256-row K-major operand)
     uint8_t A[kOzStages][kOzABytes];       // 64 KB
     double xp[kOzEpiWarps][32 * 16];       // 32 KB: per epilogue warp, a 32 x 16 block of C
-    int32_t ex[2][kOzNb];                  // row exponents of A and B
+    int32_t ex[2][kOzNb];                  // [1]: column exponents (rows of B) of the current update
     OzShared os;
 };
 
@@ -186,6 +194,7 @@ inline __device__ void oz_cta_init(OzShared &os) {
         os.ring = 0;
         os.quarters = 0;
         os.fail = 0;
+        os.pend = 0;
         mbar_fence_init();
     }
     if (threadIdx.x / 32 == 1) {
@@ -209,6 +218,134 @@ inline __device__ void oz_cta_fini(OzShared &os) {
     if (threadIdx.x / 32 == 1) tmem_dealloc(os.tmem_base, 512);
 }
 
+// One quarter of the epilogue for one epilogue warp (ew = warp - 4): rows of
+// lane quadrant q = warp & 3, columns col0 .. col0 + 15 with col0 = 32 qq +
+// 16 (ew >> 2), accumulators in tensor-memory half u & 1 of quarter u.  ea is
+// the exponent of this lane's row, exB the column exponents of the tile.
+// Returns false if the wait for the accumulators expired.
+__device__ inline bool oz_epilogue_quarter(OzSmem &sm, double *C, int qq, uint32_t u, int ea, const int32_t *exB,
+                                           uint64_t deadline) {
+    OzShared &os = sm.os;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int ew = warp - 4, q = warp & 3, ch = ew >> 2;
+    const uint32_t b = u & 1;
+    double *xp = sm.xp[ew];
+    const int col0 = qq * kOzQ + ch * 16;
+    // stage this warp's 32 x 16 block of C in shared memory (async, coalesced
+    // 16-byte copies) while the accumulators are produced
+    double *cblk = C + (size_t)(q * 32) * kOzNb + col0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int idx = i * 32 + lane, rr = idx >> 3, seg = idx & 7;
+        cp_async16(smem_u32(xp + xp_idx(rr, 2 * seg)), cblk + (size_t)rr * kOzNb + 2 * seg);
+    }
+    int eb[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) eb[j] = ea + exB[col0 + j];
+    // one lane polls, the others wait at the shuffle
+    bool got = true;
+    if (lane == 0) got = mbar_wait(&os.acc_full[b], (u >> 1) & 1, deadline);
+    got = __shfl_sync(0xffffffffu, got, 0);
+    if (!got) {
+        cp_async_wait_all();
+        return false;
+    }
+    tc_fence_after();
+    // group d = g + 2 holds at most d - 1 products below 2^21 each, so
+    // G_{2k} 128 + G_{2k+1} fits in int32; hi = (t01 << 14) + t23 and
+    // lo = (t45 << 14) + t67 are exact int64.
+    long long hi[16], lo[16];
+    const uint32_t tb = os.tmem_base + ((uint32_t)(q * 32) << 16) + b * (uint32_t)(kOzS * kOzQ) + (uint32_t)(ch * 16);
+#pragma unroll
+    for (int half4 = 0; half4 < 2; ++half4) {
+        uint32_t r0[16], r1[16], r2[16], r3[16];
+        const int g = half4 * 4;
+        tmem_ld16(tb + (uint32_t)(g * kOzQ), r0);
+        tmem_ld16(tb + (uint32_t)((g + 1) * kOzQ), r1);
+        tmem_ld16(tb + (uint32_t)((g + 2) * kOzQ), r2);
+        tmem_ld16(tb + (uint32_t)((g + 3) * kOzQ), r3);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int32_t t01 = __float2int_rn(__uint_as_float(r0[j])) * 128 + __float2int_rn(__uint_as_float(r1[j]));
+            const int32_t t23 = __float2int_rn(__uint_as_float(r2[j])) * 128 + __float2int_rn(__uint_as_float(r3[j]));
+            const long long w = ((long long)t01 << 14) + (long long)t23;
+            if (half4 == 0) hi[j] = w;
+            else lo[j] = w;
+        }
+    }
+    // the accumulators are in registers: release this half of tensor memory
+    // to the MMAs of quarter u + 2 before updating C
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&os.tmem_empty[b]);
+    // one vote per quarter: exponents of the scaled values stay normal
+    // (|hi|, |lo| < 2^47) unless a row or column scale is extreme
+    bool ok_range = true;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) ok_range &= (eb[j] >= -900 && eb[j] <= 900);
+    cp_async_wait_all();
+    __syncwarp();
+    // this lane's row of the block: C <- (C - hi 2^(eab-35)) - lo 2^(eab-63)
+    if (__all_sync(0xffffffffu, ok_range)) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            double &cv = xp[xp_idx(lane, j)];
+            cv = (cv - int_scaled_fast(hi[j], eb[j] - 35)) - int_scaled_fast(lo[j], eb[j] - 63);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            double &cv = xp[xp_idx(lane, j)];
+            cv = (cv - int_scaled(hi[j], eb[j] - 35)) - int_scaled(lo[j], eb[j] - 63);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int idx = i * 32 + lane, rr = idx >> 3, seg = idx & 7;
+        const double2 v = *reinterpret_cast<const double2 *>(xp + xp_idx(rr, 2 * seg));
+        *reinterpret_cast<double2 *>(cblk + (size_t)rr * kOzNb + 2 * seg) = v;
+    }
+    __syncwarp();
+    return true;
+}
+
+// The epilogue warps apply the deferred quarter, if any, then one thread
+// hands its word to on_done (after all 8 warps' stores: the named barrier).
+template <class Done>
+__device__ inline bool oz_epilogue_pending(OzSmem &sm, uint64_t deadline, const Done &on_done) {
+    OzShared &os = sm.os;
+    if (!os.pend) return true;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int row = (warp & 3) * 32 + lane;
+    const bool ok = oz_epilogue_quarter(sm, os.pend_C, kOzNb / kOzQ - 1, os.pend_u, __ldcg(os.pend_expA + row),
+                                        os.pend_expB, deadline);
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps only
+    if (warp == 4 && lane == 0 && ok) on_done(os.pend_task, os.pend_t0);
+    return ok;
+}
+
+struct OzNoDone {
+    __device__ void operator()(uint64_t, uint64_t) const {}
+};
+
+// Apply a deferred last quarter now (all threads of the CTA; ends with a
+// barrier).  False if a wait expired.
+template <class Done>
+__device__ inline bool ozaki_flush(OzSmem &sm, uint64_t timeout_ns, const Done &on_done) {
+    OzShared &os = sm.os;
+    bool ok = true;
+    if (threadIdx.x >= 128) ok = oz_epilogue_pending(sm, global_ns() + timeout_ns, on_done);
+    if (!ok) oz_fail(os);
+    __syncthreads();
+    ok = !oz_failed(os);
+    __syncthreads();
+    if (threadIdx.x == 0) os.pend = 0;
+    __syncthreads();
+    return ok;
+}
+
 // C (row-major 128 x 128 binary64) -= A B^T where A, B are given by their
 // slices: rows [aRow0, aRow0 + 8*128) and [bRow0, ...) of the slice maps
 // (slice s of a tile at rows base + 128 s) and their row exponents.  mapA has
@@ -222,10 +359,16 @@ struct OzNoHook {
     __device__ void operator()() const {}
 };
 
-template <class Hook = OzNoHook>
+//
+// A deferred quarter of the previous call is applied first by the epilogue
+// warps (its completion handed to on_done); with defer_last this call's last
+// quarter is left for the next call or ozaki_flush, tagged with `task`/t0.
+template <class Hook = OzNoHook, class Done = OzNoDone>
 __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, const CUtensorMap *mapB, double *C,
                                          int aRow0, int bRow0, const int32_t *expA, const int32_t *expB,
-                                         uint64_t timeout_ns, const Hook &producer_idle = Hook()) {
+                                         uint64_t timeout_ns, const Hook &producer_idle = Hook(),
+                                         const Done &on_done = Done(), bool defer_last = false, uint64_t task = 0,
+                                         uint64_t t0 = 0) {
     OzShared &os = sm.os;
     const uint32_t ring0 = os.ring, q0 = os.quarters;
     const uint64_t deadline = global_ns() + timeout_ns;
@@ -315,114 +458,24 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
         // and lo = sum_{g>=4} G_g 2^{7(7-g)} are exact int64 (< 2^46); the
         // update is A B^T = 2^{e_r + e_c} (hi 2^-35 + lo 2^-63).  Warp w owns
         // the 32 rows of lane quadrant w % 4 and columns 16 ((w - 4) / 4) ..
-        // +15 of each quarter; it stages its 32 x 16 block of C in shared memory
-        // with coalesced asynchronous copies, each lane (one row) applies its
-        // row's update there, and the block is written back coalesced.
-        const int ew = warp - 4;
-        const int q = warp & 3;
-        const int ch = ew >> 2;
-        const int row = q * 32 + lane;
+        // +15 of each quarter (oz_epilogue_quarter).
+        const int row = (warp & 3) * 32 + lane;
         // pull this row of C into L2 while the MMAs run (8 lines of 128 bytes)
-        if (ch == 0) {
+        if (warp < 8) {
 #pragma unroll
             for (int l = 0; l < 8; ++l)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (size_t)row * kOzNb + l * 16));
         }
-        for (int i = threadIdx.x - 128; i < kOzNb; i += 32 * kOzEpiWarps) {
-            sm.ex[0][i] = __ldcg(expA + i);
-            sm.ex[1][i] = __ldcg(expB + i);
-        }
+        // the previous call's deferred quarter (its accumulators are in the
+        // other tensor-memory half than this call's first quarter)
+        bool ok = oz_epilogue_pending(sm, deadline, on_done);
+        for (int i = threadIdx.x - 128; i < kOzNb; i += 32 * kOzEpiWarps) sm.ex[1][i] = __ldcg(expB + i);
+        const int ea = __ldcg(expA + row);
         asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps only
-        const int ea = sm.ex[0][row];
-        double *xp = sm.xp[ew];
+        const int nq = defer_last ? kQuarters - 1 : kQuarters;
 #pragma unroll 1
-        for (int qq = 0; qq < kQuarters; ++qq) {
-            const uint32_t u = q0 + qq, b = u & 1;
-            const int col0 = qq * kOzQ + ch * 16;  // first tile column of this warp's block
-            // stage this warp's 32 x 16 block of C in shared memory (async,
-            // coalesced 16-byte copies) while the accumulators are produced
-            double *cblk = C + (size_t)(q * 32) * kOzNb + col0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int idx = i * 32 + lane, rr = idx >> 3, seg = idx & 7;
-                cp_async16(smem_u32(xp + xp_idx(rr, 2 * seg)), cblk + (size_t)rr * kOzNb + 2 * seg);
-            }
-            // one lane polls, the others wait at the shuffle
-            bool got = true;
-            if (lane == 0) got = mbar_wait(&os.acc_full[b], (u >> 1) & 1, deadline);
-            got = __shfl_sync(0xffffffffu, got, 0);
-            if (!got) {
-                oz_fail(os);
-                cp_async_wait_all();
-                break;
-            }
-            tc_fence_after();
-            // group d = g + 2 holds at most d - 1 products below 2^21 each, so
-            // G_{2k} 128 + G_{2k+1} fits in int32; hi = (t01 << 14) + t23 and
-            // lo = (t45 << 14) + t67 are exact int64.
-            long long hi[16], lo[16];
-            const uint32_t tb =
-                os.tmem_base + ((uint32_t)(q * 32) << 16) + b * (uint32_t)(kOzS * kOzQ) + (uint32_t)(ch * 16);
-#pragma unroll
-            for (int half4 = 0; half4 < 2; ++half4) {
-                uint32_t r0[16], r1[16], r2[16], r3[16];
-                const int g = half4 * 4;
-                tmem_ld16(tb + (uint32_t)(g * kOzQ), r0);
-                tmem_ld16(tb + (uint32_t)((g + 1) * kOzQ), r1);
-                tmem_ld16(tb + (uint32_t)((g + 2) * kOzQ), r2);
-                tmem_ld16(tb + (uint32_t)((g + 3) * kOzQ), r3);
-                tmem_ld_wait();
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int32_t t01 = __float2int_rn(__uint_as_float(r0[j])) * 128 +
-                                        __float2int_rn(__uint_as_float(r1[j]));
-                    const int32_t t23 = __float2int_rn(__uint_as_float(r2[j])) * 128 +
-                                        __float2int_rn(__uint_as_float(r3[j]));
-                    const long long w = ((long long)t01 << 14) + (long long)t23;
-                    if (half4 == 0) hi[j] = w;
-                    else lo[j] = w;
-                }
-            }
-            // the accumulators are in registers: release this half of tensor
-            // memory to the MMAs of quarter u + 2 before updating C
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&os.tmem_empty[b]);
-            // one vote per quarter: exponents of the scaled values stay normal
-            // (|hi|, |lo| < 2^47) unless a row or column scale is extreme
-            bool ok_range = true;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int eab = ea + sm.ex[1][col0 + j];
-                ok_range &= (eab >= -900 && eab <= 900);
-            }
-            cp_async_wait_all();
-            __syncwarp();
-            // this lane's row of the block: C <- (C - hi 2^(eab-35)) - lo 2^(eab-63)
-            if (__all_sync(0xffffffffu, ok_range)) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int eab = ea + sm.ex[1][col0 + j];
-                    double &cv = xp[xp_idx(lane, j)];
-                    cv = (cv - int_scaled_fast(hi[j], eab - 35)) - int_scaled_fast(lo[j], eab - 63);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int eab = ea + sm.ex[1][col0 + j];
-                    double &cv = xp[xp_idx(lane, j)];
-                    cv = (cv - int_scaled(hi[j], eab - 35)) - int_scaled(lo[j], eab - 63);
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int idx = i * 32 + lane, rr = idx >> 3, seg = idx & 7;
-                const double2 v = *reinterpret_cast<const double2 *>(xp + xp_idx(rr, 2 * seg));
-                *reinterpret_cast<double2 *>(cblk + (size_t)rr * kOzNb + 2 * seg) = v;
-            }
-            __syncwarp();
-        }
+        for (int qq = 0; qq < nq && ok; ++qq) ok = oz_epilogue_quarter(sm, C, qq, q0 + qq, ea, sm.ex[1], deadline);
+        if (!ok) oz_fail(os);
     }
     __syncthreads();
     const bool ok = !oz_failed(os);
@@ -430,6 +483,15 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
     if (threadIdx.x == 0 && ok) {
         os.ring = ring0 + kQuarters * kOzS;
         os.quarters = q0 + kQuarters;
+        os.pend = defer_last ? 1 : 0;
+        if (defer_last) {
+            os.pend_u = q0 + kQuarters - 1;
+            os.pend_C = C;
+            os.pend_expA = expA;
+            os.pend_expB = expB;
+            os.pend_task = task;
+            os.pend_t0 = t0;
+        }
     }
     __syncthreads();
     return ok;
