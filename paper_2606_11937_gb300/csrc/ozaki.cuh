@@ -71,7 +71,7 @@ struct OzSmem {
                                            // 8 slices of a K-chunk form one 256-row K-major operand)
     uint8_t A[kOzStages][kOzABytes];       // 64 KB
     double xp[kOzEpiWarps][32 * 16];       // 32 KB: per epilogue warp, a 32 x 16 block of C
-    int32_t ex[2][kOzNb];                  // [1]: column exponents (rows of B) of the current update
+    int32_t ex[2][kOzNb];                  // column exponents (rows of B): [1] current update, [0] deferred quarter
     OzShared os;
 };
 
@@ -221,7 +221,8 @@ inline __device__ void oz_cta_fini(OzShared &os) {
 // One quarter of the epilogue for one epilogue warp (ew = warp - 4): rows of
 // lane quadrant q = warp & 3, columns col0 .. col0 + 15 with col0 = 32 qq +
 // 16 (ew >> 2), accumulators in tensor-memory half u & 1 of quarter u.  ea is
-// the exponent of this lane's row, exB the column exponents of the tile.
+// the exponent of this lane's row, exB the column exponents of the tile (in
+// shared memory).
 // Returns false if the wait for the accumulators expired.
 __device__ inline bool oz_epilogue_quarter(OzSmem &sm, double *C, int qq, uint32_t u, int ea, const int32_t *exB,
                                            uint64_t deadline) {
@@ -239,9 +240,6 @@ __device__ inline bool oz_epilogue_quarter(OzSmem &sm, double *C, int qq, uint32
         const int idx = i * 32 + lane, rr = idx >> 3, seg = idx & 7;
         cp_async16(smem_u32(xp + xp_idx(rr, 2 * seg)), cblk + (size_t)rr * kOzNb + 2 * seg);
     }
-    int eb[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) eb[j] = ea + exB[col0 + j];
     // one lane polls, the others wait at the shuffle
     bool got = true;
     if (lane == 0) got = mbar_wait(&os.acc_full[b], (u >> 1) & 1, deadline);
@@ -283,21 +281,26 @@ __device__ inline bool oz_epilogue_quarter(OzSmem &sm, double *C, int qq, uint32
     // (|hi|, |lo| < 2^47) unless a row or column scale is extreme
     bool ok_range = true;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) ok_range &= (eb[j] >= -900 && eb[j] <= 900);
+    for (int j = 0; j < 16; ++j) {
+        const int e = ea + exB[col0 + j];
+        ok_range &= (e >= -900 && e <= 900);
+    }
     cp_async_wait_all();
     __syncwarp();
     // this lane's row of the block: C <- (C - hi 2^(eab-35)) - lo 2^(eab-63)
     if (__all_sync(0xffffffffu, ok_range)) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
+            const int e = ea + exB[col0 + j];
             double &cv = xp[xp_idx(lane, j)];
-            cv = (cv - int_scaled_fast(hi[j], eb[j] - 35)) - int_scaled_fast(lo[j], eb[j] - 63);
+            cv = (cv - int_scaled_fast(hi[j], e - 35)) - int_scaled_fast(lo[j], e - 63);
         }
     } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
+            const int e = ea + exB[col0 + j];
             double &cv = xp[xp_idx(lane, j)];
-            cv = (cv - int_scaled(hi[j], eb[j] - 35)) - int_scaled(lo[j], eb[j] - 63);
+            cv = (cv - int_scaled(hi[j], e - 35)) - int_scaled(lo[j], e - 63);
         }
     }
     __syncwarp();
@@ -319,8 +322,12 @@ __device__ inline bool oz_epilogue_pending(OzSmem &sm, uint64_t deadline, const 
     if (!os.pend) return true;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int row = (warp & 3) * 32 + lane;
+    // the deferred quarter's column exponents go to ex[0] (unused otherwise)
+    const int c0 = kOzNb - kOzQ;
+    if (threadIdx.x - 128 < kOzQ) sm.ex[0][c0 + threadIdx.x - 128] = __ldcg(os.pend_expB + c0 + threadIdx.x - 128);
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps only
     const bool ok = oz_epilogue_quarter(sm, os.pend_C, kOzNb / kOzQ - 1, os.pend_u, __ldcg(os.pend_expA + row),
-                                        os.pend_expB, deadline);
+                                        sm.ex[0], deadline);
     asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps only
     if (warp == 4 && lane == 0 && ok) on_done(os.pend_task, os.pend_t0);
     return ok;
