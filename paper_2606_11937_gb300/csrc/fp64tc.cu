@@ -35,6 +35,163 @@ struct OzArgs {
     uint64_t timeout_ns;
 };
 
+// Cholesky of a 128 x 128 diagonal tile (row-major, lower part read and
+// written) in shared memory, right-looking: columns are factored four at a
+// time and each block of four is applied to the trailing lower triangle as
+// one rank-4 update.  Every element sees the same operations in the same
+// order as the Crout formulas (fused multiply-subtracts in ascending column
+// order, division by the pivot).  The trailing elements are visited through a
+// table of (i, k) in column-major lower order, so the active ones form a
+// contiguous suffix and all threads stay busy.  All threads; uses the B and A
+// regions of the shared memory; returns 0 or the 1-based local column whose
+// pivot is not positive (or NaN).  Ends with a barrier.
+static_assert((size_t)kOzNb * (kOzNb + 1) * 8 + (size_t)kOzNb * (kOzNb + 1) <= sizeof(OzSmem::B) + sizeof(OzSmem::A),
+              "the padded tile and its index table must fit in the B and A regions");
+__device__ int oz_potrf128(double *A, OzSmem &sm) {
+    constexpr int P = kOzNb + 1;  // padded row
+    double *S = reinterpret_cast<double *>(sm.B);
+    uint16_t *tab = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(sm.B) + kOzNb * P * 8);
+    const int t = threadIdx.x, nt = blockDim.x;
+    constexpr int kTri = kOzNb * (kOzNb + 1) / 2;
+    for (int e = t; e < kOzNb * kOzNb; e += nt) {
+        const int i = e / kOzNb, k = e % kOzNb;
+        if (k <= i) S[i * P + k] = __ldcg(A + e);
+    }
+    for (int k = t; k < kOzNb; k += nt) {
+        const int off = k * kOzNb - k * (k - 1) / 2;
+        for (int i = k; i < kOzNb; ++i) tab[off + i - k] = (uint16_t)((i << 8) | k);
+    }
+    __syncthreads();
+    for (int j0 = 0; j0 < kOzNb; j0 += 4) {
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q;
+            const double djj = S[j * P + j];
+            if (!(djj > 0.0)) {  // uniform: every thread read the same value
+                __syncthreads();
+                return j + 1;
+            }
+            const double d = sqrt(djj);
+            for (int i = j + 1 + t; i < kOzNb; i += nt) S[i * P + j] = S[i * P + j] / d;
+            __syncthreads();
+            if (t == 0) S[j * P + j] = d;
+            // the rest of the panel: columns c = j+1 .. j0+3, rows i >= c
+            const int nc = j0 + 3 - j;
+            for (int e = t; e < nc * kOzNb; e += nt) {
+                const int c = j + 1 + e / kOzNb, i = e % kOzNb;
+                if (i >= c) S[i * P + c] = fma(-S[i * P + j], S[c * P + j], S[i * P + c]);
+            }
+            __syncthreads();
+        }
+        // trailing rank-4 update of the elements (i, k), j0 + 4 <= k <= i
+        const int k0 = j0 + 4;
+        const int off = k0 * kOzNb - k0 * (k0 - 1) / 2;
+        for (int e = off + t; e < kTri; e += nt) {
+            const int ik = tab[e], i = ik >> 8, k = ik & 255;
+            double v = S[i * P + k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v = fma(-S[i * P + j0 + q], S[k * P + j0 + q], v);
+            S[i * P + k] = v;
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < kOzNb * kOzNb; e += nt) {
+        const int i = e / kOzNb, k = e % kOzNb;
+        if (k <= i) A[e] = S[i * P + k];
+    }
+    __syncthreads();
+    return 0;
+}
+
+// Inverse W = L^{-1} of the lower triangular factor that oz_potrf128 left in
+// shared memory (lower part of the padded square S, kept intact), by forward
+// substitution on the identity in blocks of four rows: the rows k0..k0+3 of
+// W are finished one after the other (entry (k, c) = (R(k, c) - sum over
+// m = k0..k-1 of L(k, m) W(m, c)) / L(k, k), R the updated right-hand side),
+// then the rows below receive them as one rank-4 update R(i, c) -=
+// sum_q L(i, k0+q) W(k0+q, c).  W(i, c), c < i, is stored transposed in the
+// strict upper part of S (S(c, i)), its diagonal in a separate vector.  Writes
+// W (row-major, zero above the diagonal) to Wout and returns
+// kappa_inf = ||L||_inf ||W||_inf.  All threads; ends with a barrier.
+__device__ double oz_trtri128(OzSmem &sm, double *Wout) {
+    constexpr int P = kOzNb + 1;
+    double *S = reinterpret_cast<double *>(sm.B);
+    double *wd = sm.xp[0];           // diagonal of W
+    double *red = sm.xp[1];          // row-sum maxima
+    const int t = threadIdx.x, nt = blockDim.x, warp = t / 32, lane = t % 32, nw = nt / 32;
+    // ||L||_inf (row sums of |L|); R = I in the strict upper part (zeros)
+    double m = 0.0;
+    for (int i = t; i < kOzNb; i += nt) {
+        double r = 0.0;
+        for (int k = 0; k <= i; ++k) r += fabs(S[i * P + k]);
+        m = fmax(m, r);
+    }
+    for (int e = t; e < kOzNb * kOzNb; e += nt) {
+        const int c = e / kOzNb, i = e % kOzNb;
+        if (c < i) S[c * P + i] = 0.0;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    double nL = 0.0;
+    for (int w = 0; w < nw; ++w) nL = fmax(nL, red[w]);
+    for (int k0 = 0; k0 < kOzNb; k0 += 4) {
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 + q;
+            // row k of W: entries c < k from R(k, c) (= S(c, k)), the diagonal 1 / L(k, k)
+            for (int c = t; c <= k; c += nt) {
+                if (c == k) {
+                    wd[k] = 1.0 / S[k * P + k];
+                } else {
+                    double v = S[c * P + k];
+                    for (int mm = k0; mm < k; ++mm) {
+                        const double wmc = c < mm ? S[c * P + mm] : (c == mm ? wd[mm] : 0.0);
+                        v = fma(-S[k * P + mm], wmc, v);
+                    }
+                    S[c * P + k] = v / S[k * P + k];
+                }
+            }
+            __syncthreads();
+        }
+        // rows i >= k0 + 4, columns c <= k0 + 3: R(i, c) -= sum_q L(i, k0+q) W(k0+q, c)
+        const int i0 = k0 + 4;
+        if (i0 < kOzNb) {
+            for (int c = warp; c < i0; c += nw) {
+                double wq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = k0 + q;
+                    wq[q] = c < r ? S[c * P + r] : (c == r ? wd[r] : 0.0);
+                }
+                for (int i = i0 + lane; i < kOzNb; i += 32) {
+                    double v = S[c * P + i];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v = fma(-S[i * P + k0 + q], wq[q], v);
+                    S[c * P + i] = v;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // ||W||_inf, and W out
+    m = 0.0;
+    for (int i = t; i < kOzNb; i += nt) {
+        double r = fabs(wd[i]);
+        for (int c = 0; c < i; ++c) r += fabs(S[c * P + i]);
+        m = fmax(m, r);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[16 + warp] = m;
+    for (int e = t; e < kOzNb * kOzNb; e += nt) {
+        const int i = e / kOzNb, c = e % kOzNb;
+        Wout[e] = c < i ? S[c * P + i] : (c == i ? wd[i] : 0.0);
+    }
+    __syncthreads();
+    double nW = 0.0;
+    for (int w = 0; w < nw; ++w) nW = fmax(nW, red[16 + w]);
+    __syncthreads();
+    return nL * nW;
+}
+
 // Largest infinity-norm condition number ||L_JJ|| ||L_JJ^{-1}|| for which the
 // TRSMs of block column J multiply by the inverse (the error of X W^T grows
 // with it); a worse-conditioned diagonal tile keeps the substitution TRSM.
@@ -122,37 +279,21 @@ struct OzBody {
         if (!(a.flags & CHOL_FLAG_NOOP)) {
             switch (type) {
             case T_POTRF: {
-                // the tile routines run on threads 0..255; the others wait at the barriers
-                __shared__ int s_li, s_use_w;
-                if (threadIdx.x < kThreads) {
-                    const int li = tile_potrf(S.tile(J, J), kOzNb, ss);
-                    if (threadIdx.x == 0) s_li = li;
-                }
-                __syncthreads();
-                const int li = s_li;
+                const int li = oz_potrf128(S.tile(J, J), sm);
                 if (li) {
                     if (threadIdx.x == 0) {
                         report_info(a.ctl, (int64_t)J * kOzNb + li);
                         st_release_s32(&a.ctl->abort, 1);
                     }
                 } else if (J < S.M - 1) {
-                    // W_J = L_JJ^{-1} for the TRSMs of this block column:
-                    // Y = I L_JJ^{-T} by the substitution kernel, then the
-                    // slices of W_J = Y^T (rows of W_J are the columns of Y)
-                    double *Y = g.wbuf + (size_t)J * kOzNb * kOzNb;
-                    for (int e = threadIdx.x; e < kOzNb * kOzNb; e += blockDim.x)
-                        Y[e] = (e / kOzNb == e % kOzNb) ? 1.0 : 0.0;
-                    __syncthreads();
-                    if (threadIdx.x < kThreads) {
-                        tile_trsm(Y, S.tile(J, J), kOzNb, ss, true);
-                        const double kappa = oz_kappa_inf(S.tile(J, J), Y, sm.xp[0]);
-                        if (threadIdx.x == 0) s_use_w = kappa <= kTrsmKappa;  // false also for a NaN
-                    }
-                    __syncthreads();
-                    const bool use_w = s_use_w != 0;
+                    // W_J = L_JJ^{-1} for the TRSMs of this block column, from
+                    // the factor still in shared memory; its slices (rows of W_J)
+                    // when it is well conditioned
+                    double *W = g.wbuf + (size_t)J * kOzNb * kOzNb;
+                    const double kappa = oz_trtri128(sm, W);
+                    const bool use_w = kappa <= kTrsmKappa;  // false also for a NaN
                     if (use_w)
-                        ozaki_split(Y, g.wslices + (size_t)J * kOzS * kOzNb * kOzNb, g.wexp + (size_t)J * kOzNb,
-                                    false, true);
+                        ozaki_split(W, g.wslices + (size_t)J * kOzS * kOzNb * kOzNb, g.wexp + (size_t)J * kOzNb);
                     if (threadIdx.x == 0) g.wflag[J] = use_w ? 1 : 0;
                 }
             } break;
