@@ -1,10 +1,11 @@
 // fp64tc.cu -- FP64 factorization whose SYRK/GEMM run on the tensor cores with
 // binary64 accuracy (exact bf16 slicing, ozaki.cuh).  POTRF stays on the CUDA
-// cores in binary64 and also forms W_J = L_JJ^{-1} by substitution; the TRSMs
-// of block column J are then one emulated product A_IJ W_J^T each on the
-// tensor cores, unless L_JJ is ill-conditioned (kappa_inf above kTrsmKappa),
-// when they keep the substitution kernel.  Selected with CHOL_FLAG_FP64_TC;
-// tiles of order 128.  Both schedules of Section 3.2 run this body unchanged.
+// cores in binary64 (the tile in shared memory) and also forms the inverse
+// W_J = L_JJ^{-1} there; the TRSMs of block column J are then one emulated
+// product A_IJ W_J^T each on the tensor cores, unless L_JJ is ill-conditioned
+// (kappa_inf above kTrsmKappa), when they keep the substitution kernel.
+// Selected with CHOL_FLAG_FP64_TC; tiles of order 128.  Both schedules of
+// Section 3.2 run this body unchanged.
 #include <cuda.h>
 #include <string.h>
 
@@ -196,36 +197,6 @@ __device__ double oz_trtri128(OzSmem &sm, double *Wout) {
 // TRSMs of block column J multiply by the inverse (the error of X W^T grows
 // with it); a worse-conditioned diagonal tile keeps the substitution TRSM.
 constexpr double kTrsmKappa = 65536.0;
-
-// kappa_inf(L) = max_r sum_c |L_rc| * max_c sum_r |Y_rc| for the lower
-// triangular L and Y = L^{-T} (row sums of L^{-1} are column sums of Y).
-// Threads 0..255 (simt_sync); the result is valid in each of them.
-__device__ double oz_kappa_inf(const double *L, const double *Y, double *red) {
-    double mL = 0.0, mY = 0.0;
-    for (int i = threadIdx.x; i < kOzNb; i += kThreads) {
-        double sl = 0.0, sy = 0.0;
-        for (int c = 0; c <= i; ++c) sl += fabs(__ldcg(L + (size_t)i * kOzNb + c));
-        for (int r = 0; r <= i; ++r) sy += fabs(__ldcg(Y + (size_t)r * kOzNb + i));
-        mL = fmax(mL, sl);
-        mY = fmax(mY, sy);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        mL = fmax(mL, __shfl_xor_sync(0xffffffffu, mL, o));
-        mY = fmax(mY, __shfl_xor_sync(0xffffffffu, mY, o));
-    }
-    if (threadIdx.x % 32 == 0) {
-        red[threadIdx.x / 32] = mL;
-        red[8 + threadIdx.x / 32] = mY;
-    }
-    simt_sync();
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) {
-        a = fmax(a, red[w]);
-        b = fmax(b, red[8 + w]);
-    }
-    simt_sync();
-    return a * b;
-}
 
 struct OzBody {
     using Args = OzArgs;

@@ -173,20 +173,15 @@ __device__ void rows_trsm(T *P, int ld, int jb, int w, int r0, int r1, SimtSmem<
 }
 
 // A_IJ <- A_IJ L^{-T}: blocked right-looking over panels of kIB columns.
-// With `upper` the caller promises that row r of B is zero left of column r
-// (B = I gives L^{-T}, which keeps that shape): a panel then touches only the
-// rows above its last column, about half the work.
 template <typename T>
-__device__ void tile_trsm(T *B, const T *L, int nb, SimtSmem<T> &sm, bool upper = false) {
+__device__ void tile_trsm(T *B, const T *L, int nb, SimtSmem<T> &sm) {
     for (int jb = 0; jb < nb; jb += kIB) {
         const int w = min(kIB, nb - jb);
-        const int rows = upper ? jb + w : nb;
         stage_diag(L, nb, jb, w, sm);
-        rows_trsm(B, nb, jb, w, 0, rows, sm);
+        rows_trsm(B, nb, jb, w, 0, nb, sm);
         const int c0 = jb + w;
         if (c0 < nb)
-            region_nt_update<T, false>(B + c0, nb, B + jb, nb, L + (size_t)c0 * nb + jb, nb, rows,
-                                       nb - c0, w, sm);
+            region_nt_update<T, false>(B + c0, nb, B + jb, nb, L + (size_t)c0 * nb + jb, nb, nb, nb - c0, w, sm);
     }
 }
 
