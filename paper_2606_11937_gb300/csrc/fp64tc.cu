@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "factor_impl.cuh"
 #include "ozaki.cuh"
+#include "potrf128.cuh"
 
 namespace chol {
 
@@ -36,71 +37,12 @@ struct OzArgs {
     uint64_t timeout_ns;
 };
 
-// Cholesky of a 128 x 128 diagonal tile (row-major, lower part read and
-// written) in shared memory, right-looking: columns are factored four at a
-// time and each block of four is applied to the trailing lower triangle as
-// one rank-4 update.  Every element sees the same operations in the same
-// order as the Crout formulas (fused multiply-subtracts in ascending column
-// order, division by the pivot).  The trailing elements are visited through a
-// table of (i, k) in column-major lower order, so the active ones form a
-// contiguous suffix and all threads stay busy.  All threads; uses the B and A
-// regions of the shared memory; returns 0 or the 1-based local column whose
-// pivot is not positive (or NaN).  Ends with a barrier.
-static_assert((size_t)kOzNb * (kOzNb + 1) * 8 + (size_t)kOzNb * (kOzNb + 1) <= sizeof(OzSmem::B) + sizeof(OzSmem::A),
+// The FP64 diagonal factorization in shared memory (potrf128.cuh) over the B
+// and A regions of the tile-update staging area.
+static_assert(kPotrf128SmemBytes <= sizeof(OzSmem::B) + sizeof(OzSmem::A),
               "the padded tile and its index table must fit in the B and A regions");
-__device__ int oz_potrf128(double *A, OzSmem &sm) {
-    constexpr int P = kOzNb + 1;  // padded row
-    double *S = reinterpret_cast<double *>(sm.B);
-    uint16_t *tab = reinterpret_cast<uint16_t *>(reinterpret_cast<uint8_t *>(sm.B) + kOzNb * P * 8);
-    const int t = threadIdx.x, nt = blockDim.x;
-    constexpr int kTri = kOzNb * (kOzNb + 1) / 2;
-    for (int e = t; e < kOzNb * kOzNb; e += nt) {
-        const int i = e / kOzNb, k = e % kOzNb;
-        if (k <= i) S[i * P + k] = __ldcg(A + e);
-    }
-    for (int k = t; k < kOzNb; k += nt) {
-        const int off = k * kOzNb - k * (k - 1) / 2;
-        for (int i = k; i < kOzNb; ++i) tab[off + i - k] = (uint16_t)((i << 8) | k);
-    }
-    __syncthreads();
-    for (int j0 = 0; j0 < kOzNb; j0 += 4) {
-        for (int q = 0; q < 4; ++q) {
-            const int j = j0 + q;
-            const double djj = S[j * P + j];
-            if (!(djj > 0.0)) {  // uniform: every thread read the same value
-                __syncthreads();
-                return j + 1;
-            }
-            const double d = sqrt(djj);
-            for (int i = j + 1 + t; i < kOzNb; i += nt) S[i * P + j] = S[i * P + j] / d;
-            __syncthreads();
-            if (t == 0) S[j * P + j] = d;
-            // the rest of the panel: columns c = j+1 .. j0+3, rows i >= c
-            const int nc = j0 + 3 - j;
-            for (int e = t; e < nc * kOzNb; e += nt) {
-                const int c = j + 1 + e / kOzNb, i = e % kOzNb;
-                if (i >= c) S[i * P + c] = fma(-S[i * P + j], S[c * P + j], S[i * P + c]);
-            }
-            __syncthreads();
-        }
-        // trailing rank-4 update of the elements (i, k), j0 + 4 <= k <= i
-        const int k0 = j0 + 4;
-        const int off = k0 * kOzNb - k0 * (k0 - 1) / 2;
-        for (int e = off + t; e < kTri; e += nt) {
-            const int ik = tab[e], i = ik >> 8, k = ik & 255;
-            double v = S[i * P + k];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) v = fma(-S[i * P + j0 + q], S[k * P + j0 + q], v);
-            S[i * P + k] = v;
-        }
-        __syncthreads();
-    }
-    for (int e = t; e < kOzNb * kOzNb; e += nt) {
-        const int i = e / kOzNb, k = e % kOzNb;
-        if (k <= i) A[e] = S[i * P + k];
-    }
-    __syncthreads();
-    return 0;
+__device__ __forceinline__ int oz_potrf128(double *A, OzSmem &sm) {
+    return smem_potrf128<double>(A, reinterpret_cast<uint8_t *>(sm.B));
 }
 
 // Inverse W = L^{-1} of the lower triangular factor that oz_potrf128 left in

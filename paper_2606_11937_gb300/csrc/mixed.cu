@@ -25,6 +25,7 @@
 #include "factor_impl.cuh"
 #include "solve_impl.cuh"
 #include "tc_gemm.cuh"
+#include "potrf128.cuh"
 
 namespace chol {
 
@@ -93,6 +94,7 @@ struct MixedSmem {
     TcShared ts;
 };
 static_assert(sizeof(SimtSmem<double>) <= sizeof(MixedSmem::stages), "SIMT scratch must fit in the stage area");
+static_assert(kPotrf128SmemBytes <= sizeof(MixedSmem::stages), "the shared-memory POTRF must fit in the stage area");
 
 __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
     uint32_t r;
@@ -180,6 +182,14 @@ struct MixedBody {
         if (!(a.flags & CHOL_FLAG_NOOP)) {
             switch (type) {
             case T_POTRF: {
+                if (nb == kPotrfNb) {  // binary64 in shared memory, the stage area
+                    const int li = smem_potrf128<float>(g.S.tile(J, J), &sm.stages[0][0]);
+                    if (li && threadIdx.x == 0) {
+                        report_info(a.ctl, (int64_t)J * nb + li);
+                        st_release_s32(&a.ctl->abort, 1);
+                    }
+                    break;
+                }
                 // widen to binary64, factor, round back
                 double *D = g.scratch + (size_t)blockIdx.x * nb * nb;
                 float *T = g.S.tile(J, J);

@@ -1,0 +1,83 @@
+// potrf128.cuh -- binary64 Cholesky of one 128 x 128 diagonal tile held in
+// shared memory (the POTRF of Section 3.1 for the tensor-core engines, whose
+// CTAs have the shared memory of a whole SM).
+#pragma once
+
+#include "common.cuh"
+
+namespace chol {
+
+constexpr int kPotrfNb = 128;
+// padded 128 x 129 binary64 tile + (i, k) table of the lower triangle
+constexpr size_t kPotrf128SmemBytes = (size_t)kPotrfNb * (kPotrfNb + 1) * 8 + (size_t)kPotrfNb * (kPotrfNb + 1);
+
+// Cholesky, in binary64, of a 128 x 128 diagonal tile (row-major, lower part
+// read and written; T = double, or float widened on load and rounded on
+// store) in shared memory, right-looking: columns are factored four at a
+// time and each block of four is applied to the trailing lower triangle as
+// one rank-4 update.  Every element sees the same operations in the same
+// order as the Crout formulas (fused multiply-subtracts in ascending column
+// order, division by the pivot).  The trailing elements are visited through a
+// table of (i, k) in column-major lower order, so the active ones form a
+// contiguous suffix and all threads stay busy.  All threads; smem holds
+// kPotrf128SmemBytes (the padded tile stays there for the caller); returns 0
+// or the 1-based local column whose pivot is not positive (or NaN).  Ends with
+// a barrier.
+template <typename T>
+__device__ int smem_potrf128(T *A, uint8_t *smem) {
+    constexpr int N = kPotrfNb;
+    constexpr int P = N + 1;  // padded row
+    double *S = reinterpret_cast<double *>(smem);
+    uint16_t *tab = reinterpret_cast<uint16_t *>(smem + N * P * 8);
+    const int t = threadIdx.x, nt = blockDim.x;
+    constexpr int kTri = N * (N + 1) / 2;
+    for (int e = t; e < N * N; e += nt) {
+        const int i = e / N, k = e % N;
+        if (k <= i) S[i * P + k] = (double)__ldcg(A + e);
+    }
+    for (int k = t; k < N; k += nt) {
+        const int off = k * N - k * (k - 1) / 2;
+        for (int i = k; i < N; ++i) tab[off + i - k] = (uint16_t)((i << 8) | k);
+    }
+    __syncthreads();
+    for (int j0 = 0; j0 < N; j0 += 4) {
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q;
+            const double djj = S[j * P + j];
+            if (!(djj > 0.0)) {  // uniform: every thread read the same value
+                __syncthreads();
+                return j + 1;
+            }
+            const double d = sqrt(djj);
+            for (int i = j + 1 + t; i < N; i += nt) S[i * P + j] = S[i * P + j] / d;
+            __syncthreads();
+            if (t == 0) S[j * P + j] = d;
+            // the rest of the panel: columns c = j+1 .. j0+3, rows i >= c
+            const int nc = j0 + 3 - j;
+            for (int e = t; e < nc * N; e += nt) {
+                const int c = j + 1 + e / N, i = e % N;
+                if (i >= c) S[i * P + c] = fma(-S[i * P + j], S[c * P + j], S[i * P + c]);
+            }
+            __syncthreads();
+        }
+        // trailing rank-4 update of the elements (i, k), j0 + 4 <= k <= i
+        const int k0 = j0 + 4;
+        const int off = k0 * N - k0 * (k0 - 1) / 2;
+        for (int e = off + t; e < kTri; e += nt) {
+            const int ik = tab[e], i = ik >> 8, k = ik & 255;
+            double v = S[i * P + k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v = fma(-S[i * P + j0 + q], S[k * P + j0 + q], v);
+            S[i * P + k] = v;
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < N * N; e += nt) {
+        const int i = e / N, k = e % N;
+        if (k <= i) A[e] = (T)S[i * P + k];
+    }
+    __syncthreads();
+    return 0;
+}
+
+}  // namespace chol
