@@ -90,7 +90,7 @@ __device__ double oz_trtri128(OzSmem &sm, double *Wout) {
                         const double wmc = c < mm ? S[c * P + mm] : (c == mm ? wd[mm] : 0.0);
                         v = fma(-S[k * P + mm], wmc, v);
                     }
-                    S[c * P + k] = v / S[k * P + k];
+                    S[c * P + k] = v * (1.0 / S[k * P + k]);
                 }
             }
             __syncthreads();

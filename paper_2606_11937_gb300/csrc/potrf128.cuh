@@ -17,7 +17,7 @@ constexpr size_t kPotrf128SmemBytes = (size_t)kPotrfNb * (kPotrfNb + 1) * 8 + (s
 // time and each block of four is applied to the trailing lower triangle as
 // one rank-4 update.  Every element sees the same operations in the same
 // order as the Crout formulas (fused multiply-subtracts in ascending column
-// order, division by the pivot).  The trailing elements are visited through a
+// order), the division by the pivot being a multiplication by its reciprocal.  The trailing elements are visited through a
 // table of (i, k) in column-major lower order, so the active ones form a
 // contiguous suffix and all threads stay busy.  All threads; smem holds
 // kPotrf128SmemBytes (the padded tile stays there for the caller); returns 0
@@ -48,8 +48,8 @@ __device__ int smem_potrf128(T *A, uint8_t *smem) {
                 __syncthreads();
                 return j + 1;
             }
-            const double d = sqrt(djj);
-            for (int i = j + 1 + t; i < N; i += nt) S[i * P + j] = S[i * P + j] / d;
+            const double d = sqrt(djj), rd = 1.0 / d;
+            for (int i = j + 1 + t; i < N; i += nt) S[i * P + j] *= rd;
             __syncthreads();
             if (t == 0) S[j * P + j] = d;
             // the rest of the panel: columns c = j+1 .. j0+3, rows i >= c
