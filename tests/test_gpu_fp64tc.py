@@ -135,3 +135,56 @@ def test_fp64tc_inverse_trsm_parity(nugget):
         assert probe_residual(S, L) <= resid_bound(n)
         outs.append(L)
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_fp64tc_withheld_dependency_times_out():
+    """Fault made on the host, tensor-core engine: the last POTRF is never
+    released, so CTAs holding a deferred quarter complete it and then wait on
+    the queues until the bounded waits expire: CHOL_ERR_TIMEOUT, and the next
+    factorization on the same context is correct."""
+    import paper_2606_11937_gb300 as chol
+    A = matrix("gram", 1024, 1)
+    f = chol.CHOL_FLAG_FP64_TC | chol.CHOL_FLAG_PRIORITY
+    _, info, st, rc = gpu_factor(A, schedule="dataflow", flags=f | chol.CHOL_FLAG_TEST_WITHHOLD, timeout_s=0.25)
+    assert rc == chol.CHOL_ERR_TIMEOUT
+    Lref, _ = oracle_factor("gram", 1024, 1)
+    L, info, st, rc = gpu_factor(A, schedule="dataflow", flags=f)
+    assert rc == 0 and scaled_error(L, Lref, A) <= TOL_SCALED
+
+
+def test_fp64tc_trace_respects_dependencies():
+    """With deferred completions a SYRK/GEMM's record ends when its last
+    quarter is stored; every task still starts after its predecessors ended,
+    and every task appears once."""
+    import ctypes
+
+    import torch
+
+    import paper_2606_11937_gb300 as chol
+    from paper_facts import GEMM, POTRF, SYRK, TRSM
+    n = 2048
+    A = matrix("gram", n, 2)
+    m = n // 128
+    cap = sum(task_counts(m)) + 10
+    rsz = ctypes.sizeof(chol.chol_trace_rec)
+    buf = torch.zeros(cap * rsz, dtype=torch.uint8, device="cuda")
+    f = chol.CHOL_FLAG_FP64_TC | chol.CHOL_FLAG_PRIORITY
+    _, info, st, rc = gpu_factor(A, schedule="dataflow", flags=f, trace=buf.data_ptr(), trace_capacity=cap)
+    assert rc == 0 and st.trace_records == sum(task_counts(m))
+    raw = buf.cpu().numpy()[: st.trace_records * rsz]
+    rec = raw.view(np.dtype([("type", "<i4"), ("I", "<i4"), ("K", "<i4"), ("J", "<i4"), ("sm", "<i4"),
+                             ("matrix", "<i4"), ("t0", "<u8"), ("t1", "<u8")]))
+    ev = {(int(r["type"]), int(r["I"]), int(r["K"]), int(r["J"])): (int(r["t0"]), int(r["t1"])) for r in rec}
+    assert len(ev) == sum(task_counts(m))
+    for (ty, I, K, J), (t0, t1) in ev.items():
+        assert t1 >= t0
+        if ty == POTRF:
+            needs = [(SYRK, I, I, J - 1)] if J > 0 else []
+        elif ty == TRSM:
+            needs = [(POTRF, J, J, J)] + ([(GEMM, I, J, J - 1)] if J > 0 else [])
+        elif ty == SYRK:
+            needs = [(TRSM, I, J, J)] + ([(SYRK, I, I, J - 1)] if J > 0 else [])
+        else:
+            needs = [(TRSM, I, J, J), (TRSM, K, J, J)] + ([(GEMM, I, K, J - 1)] if J > 0 else [])
+        for nd in needs:
+            assert ev[nd][1] <= t0, ((ty, I, K, J), nd)
