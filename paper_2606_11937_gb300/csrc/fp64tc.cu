@@ -78,23 +78,29 @@ __device__ double oz_trtri128(OzSmem &sm, double *Wout) {
     double nL = 0.0;
     for (int w = 0; w < nw; ++w) nL = fmax(nL, red[w]);
     for (int k0 = 0; k0 < kOzNb; k0 += 4) {
-        for (int q = 0; q < 4; ++q) {
-            const int k = k0 + q;
-            // row k of W: entries c < k from R(k, c) (= S(c, k)), the diagonal 1 / L(k, k)
-            for (int c = t; c <= k; c += nt) {
-                if (c == k) {
-                    wd[k] = 1.0 / S[k * P + k];
-                } else {
-                    double v = S[c * P + k];
-                    for (int mm = k0; mm < k; ++mm) {
-                        const double wmc = c < mm ? S[c * P + mm] : (c == mm ? wd[mm] : 0.0);
-                        v = fma(-S[k * P + mm], wmc, v);
+        // rows k0 .. k0+3 of W by warp 0: lane l owns columns l, l+32, ..., so
+        // the rows of a block depend on each other only within a lane (and on
+        // the diagonal entries, ordered by the warp barriers)
+        if (warp == 0) {
+            for (int q = 0; q < 4; ++q) {
+                const int k = k0 + q;
+                const double rk = 1.0 / S[k * P + k];
+                for (int c = lane; c <= k; c += 32) {
+                    if (c == k) {
+                        wd[k] = rk;
+                    } else {
+                        double v = S[c * P + k];
+                        for (int mm = k0; mm < k; ++mm) {
+                            const double wmc = c < mm ? S[c * P + mm] : (c == mm ? wd[mm] : 0.0);
+                            v = fma(-S[k * P + mm], wmc, v);
+                        }
+                        S[c * P + k] = v * rk;
                     }
-                    S[c * P + k] = v * (1.0 / S[k * P + k]);
                 }
+                __syncwarp();
             }
-            __syncthreads();
         }
+        __syncthreads();
         // rows i >= k0 + 4, columns c <= k0 + 3: R(i, c) -= sum_q L(i, k0+q) W(k0+q, c)
         const int i0 = k0 + 4;
         if (i0 < kOzNb) {

@@ -14,8 +14,9 @@ constexpr size_t kPotrf128SmemBytes = (size_t)kPotrfNb * (kPotrfNb + 1) * 8 + (s
 // Cholesky, in binary64, of a 128 x 128 diagonal tile (row-major, lower part
 // read and written; T = double, or float widened on load and rounded on
 // store) in shared memory, right-looking: columns are factored four at a
-// time and each block of four is applied to the trailing lower triangle as
-// one rank-4 update.  Every element sees the same operations in the same
+// time (the panel by one warp, with warp barriers only) and each block of four
+// is applied to the trailing lower triangle as one rank-4 update by all
+// threads.  Every element sees the same operations in the same
 // order as the Crout formulas (fused multiply-subtracts in ascending column
 // order), the division by the pivot being a multiplication by its reciprocal.  The trailing elements are visited through a
 // table of (i, k) in column-major lower order, so the active ones form a
@@ -40,25 +41,38 @@ __device__ int smem_potrf128(T *A, uint8_t *smem) {
         for (int i = k; i < N; ++i) tab[off + i - k] = (uint16_t)((i << 8) | k);
     }
     __syncthreads();
+    __shared__ int s_fail;
+    const int warp = t / 32, lane = t % 32;
     for (int j0 = 0; j0 < N; j0 += 4) {
-        for (int q = 0; q < 4; ++q) {
-            const int j = j0 + q;
-            const double djj = S[j * P + j];
-            if (!(djj > 0.0)) {  // uniform: every thread read the same value
-                __syncthreads();
-                return j + 1;
+        // the panel (columns j0 .. j0+3, rows j0 .. N-1) by warp 0 alone: lane l
+        // owns rows l, l+32, ...; only warp barriers between the columns
+        if (warp == 0) {
+            int fail = 0;
+            for (int q = 0; q < 4 && !fail; ++q) {
+                const int j = j0 + q;
+                const double djj = S[j * P + j];
+                __syncwarp();
+                if (!(djj > 0.0)) {  // uniform: every lane read the same value
+                    fail = j + 1;
+                    break;
+                }
+                const double d = sqrt(djj), rd = 1.0 / d;
+                if (lane == 0) S[j * P + j] = d;
+                for (int i = j + 1 + lane; i < N; i += 32) S[i * P + j] *= rd;
+                __syncwarp();
+                for (int c = j + 1; c < j0 + 4; ++c) {
+                    const double scj = S[c * P + j];
+                    for (int i = c + lane; i < N; i += 32) S[i * P + c] = fma(-S[i * P + j], scj, S[i * P + c]);
+                }
+                __syncwarp();
             }
-            const double d = sqrt(djj), rd = 1.0 / d;
-            for (int i = j + 1 + t; i < N; i += nt) S[i * P + j] *= rd;
+            if (lane == 0) s_fail = fail;
+        }
+        __syncthreads();
+        if (s_fail) {
+            const int f = s_fail;
             __syncthreads();
-            if (t == 0) S[j * P + j] = d;
-            // the rest of the panel: columns c = j+1 .. j0+3, rows i >= c
-            const int nc = j0 + 3 - j;
-            for (int e = t; e < nc * N; e += nt) {
-                const int c = j + 1 + e / N, i = e % N;
-                if (i >= c) S[i * P + c] = fma(-S[i * P + j], S[c * P + j], S[i * P + c]);
-            }
-            __syncthreads();
+            return f;
         }
         // trailing rank-4 update of the elements (i, k), j0 + 4 <= k <= i
         const int k0 = j0 + 4;
