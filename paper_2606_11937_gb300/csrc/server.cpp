@@ -32,6 +32,7 @@ int fp64_factor_store(int64_t n, const double *A, int64_t lda, const chol_opts &
 int fp64_solve_store(const double *store, int64_t n, int64_t nb, double *X, int64_t ldx, int64_t nrhs,
                      cudaStream_t st, double timeout_s);
 size_t fp64_store_bytes(int64_t n, int64_t nb);
+size_t fp64tc_extra_bytes(int64_t n);
 }  // namespace chol
 
 using Clock = std::chrono::steady_clock;
@@ -69,14 +70,23 @@ size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int64_t tasks_of(int64_t M) { return M * (M + 1) * (M + 2) / 6; }
 
+// FP64 requests of order above this factor with SYRK/GEMM/TRSM on the tensor
+// cores (binary64 accuracy, tiles of 128); smaller ones on the FP64 pipe,
+// where the shorter critical path wins.  A pure function of n, so a request
+// gives the same bits alone and in a mix.
+constexpr int64_t kServeTcMinN = 4096;
+bool fp64_on_tensor_cores(int64_t n) { return n > kServeTcMinN; }
+int64_t fp64_nb(int64_t n) { return fp64_on_tensor_cores(n) ? 128 : chol_default_nb(n, CHOL_FP64); }
+
 // upper bound of the device bytes a request needs while it runs
 size_t need_bytes(const chol_request &r, bool reuse) {
     const int64_t n = r.n, nrhs = r.nrhs;
     const size_t solve_ws = 32768 + 2 * (size_t)((n + 63) / 64) * ((nrhs + 15) / 16) * 4 + 1024;
     if (r.precision == CHOL_FP64) {
         if (reuse) return a256(solve_ws);
-        const int64_t nb = chol_default_nb(n, CHOL_FP64), M = (n + nb - 1) / nb;
-        return chol::fp64_store_bytes(n, nb) + a256((size_t)tasks_of(M) * 20 + 1024) + a256(solve_ws);
+        const int64_t nb = fp64_nb(n), M = (n + nb - 1) / nb;
+        return chol::fp64_store_bytes(n, nb) + a256((size_t)tasks_of(M) * 20 + 1024) + a256(solve_ws) +
+               (fp64_on_tensor_cores(n) ? chol::fp64tc_extra_bytes(n) : 0);
     }
     const size_t ir = a256((size_t)n * nrhs * 12 + (size_t)n * 8 + 3 * (size_t)nrhs * 8 + 1024) + a256(solve_ws);
     if (reuse) return ir;
@@ -87,7 +97,7 @@ size_t need_bytes(const chol_request &r, bool reuse) {
 }
 
 size_t keep_bytes_of(const chol_request &r) {
-    if (r.precision == CHOL_FP64) return chol::fp64_store_bytes(r.n, chol_default_nb(r.n, CHOL_FP64));
+    if (r.precision == CHOL_FP64) return chol::fp64_store_bytes(r.n, fp64_nb(r.n));
     const int64_t nb = chol_default_nb(r.n, r.precision), M = (r.n + nb - 1) / nb;
     return a256((size_t)M * (M + 1) / 2 * nb * nb * 4);
 }
@@ -231,6 +241,7 @@ struct chol_server_s {
             if (!r->reuse) {
                 double *s = nullptr;
                 int64_t info = 0;
+                if (fp64_on_tensor_cores(q.n)) o.flags |= CHOL_FLAG_FP64_TC | CHOL_FLAG_PRIORITY;
                 rc = chol::fp64_factor_store(q.n, q.A, q.lda, o, &s, &nb, &info);
                 r->res.info = info;
                 if (rc == CHOL_OK && info > 0) rc = CHOL_ERR_NOT_SPD;

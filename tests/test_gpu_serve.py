@@ -24,8 +24,9 @@ def test_served_results_same_alone_and_in_mix():
     import torch
 
     import paper_2606_11937_gb300 as chol
-    sizes = [300, 1500, 64, 777, 2048, 129, 1024, 500]
-    precs = ["fp64", "fp32", "fp64", "bf16", "fp64", "tf32", "fp64", "fp16"]
+    # 5000: an FP64 request large enough for the tensor-core engine
+    sizes = [300, 1500, 64, 777, 2048, 129, 1024, 500, 5000]
+    precs = ["fp64", "fp32", "fp64", "bf16", "fp64", "tf32", "fp64", "fp16", "fp64"]
     mats = [si.gram_plus_identity(n, 200 + i) if i % 2 == 0 else si.se_covariance(n, 300 + i, nugget=1e-1)
             for i, n in enumerate(sizes)]
     rhs = [si.rhs(n, 1 + (i * 7) % 32, seed=400 + i) for i, n in enumerate(sizes)]
