@@ -111,9 +111,11 @@ int64_t chol_default_nb(int64_t n, int32_t precision) {
         if (n <= 16384) return 128;
         return 256;
     }
-    // tensor-core precisions: tiles are multiples of the 128-row MMA
-    if (n <= 8192) return 128;
-    if (n <= 32768) return 256;
+    // tensor-core precisions: tiles are multiples of the 128-row MMA; 128
+    // keeps the critical path short (binary64 POTRF in shared memory) up to
+    // order 32768, larger orders amortise per-task costs over 256 tiles
+    if (n <= 32768) return 128;
+    if (n <= 65536) return 256;
     return 512;
 }
 

@@ -167,8 +167,32 @@ struct MixedBody {
     static constexpr bool kSolveTask = false;
     static constexpr int kCtasPerSm = 1;  // one CTA owns the SM's shared memory and tensor memory
     static constexpr int kBlock = kThreads;
-    static constexpr bool kLag = false;
     static constexpr size_t kSmemBytes = sizeof(MixedSmem);
+    // In the dataflow kernel a SYRK/GEMM on tiles of order 128 leaves its
+    // epilogue to the next tile update on this CTA (its accumulator is one of
+    // two tensor-memory buffers) or to flush(); the task completes when that
+    // epilogue has stored the tile.
+    static constexpr bool kLag = true;
+    static __device__ __forceinline__ bool lagging(Smem &sm) { return sm.ts.pend != 0; }
+    static __device__ __forceinline__ bool absorbs(const Args &, int I, int K, int J) {
+        const int type = task_type(I, K, J);
+        return type == T_SYRK || type == T_GEMM;
+    }
+    struct Done {
+        const Args &g;
+        const SchedArgs &a;
+        __device__ void operator()(uint64_t w, uint64_t t0) const {
+            df_complete_lagged<MixedBody>(g, a, (int)(w >> 48), (int)((w >> 32) & 0xffff), (int)((w >> 16) & 0xffff),
+                                          (int)(w & 0xffff), t0);
+        }
+    };
+    static __device__ void flush(const Args &g, const SchedArgs &a, Smem &sm) {
+        const bool ok = tc_flush(sm.ts, sm.xpose, g.timeout_ns, Done{g, a});
+        if (!ok && threadIdx.x == 0) {
+            if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 3;
+            st_release_s32(&a.ctl->abort, 1);
+        }
+    }
     static __device__ __forceinline__ void cta_init(const Args &, Smem &sm) { tc_cta_init(sm.ts); }
     static __device__ __forceinline__ void cta_fini(const Args &, Smem &sm) { tc_cta_fini(sm.ts); }
     static __device__ __forceinline__ int tiles(const Args &g, int) { return g.S.M; }
@@ -229,7 +253,8 @@ struct MixedBody {
                 }
                 ga.idesc = make_idesc((uint32_t)g.fmt, 128, nb >= 256 ? 256 : 128);
                 const bool ok = tc_tile_update(sm.ts, &sm.stages[0][0], sm.xpose, ga, g.S.tile(I, K), nb,
-                                               (int)(ta * nb), (int)(tb * nb), sa, sb, type == T_SYRK, g.timeout_ns);
+                                               (int)(ta * nb), (int)(tb * nb), sa, sb, type == T_SYRK, g.timeout_ns,
+                                               Done{g, a}, a.dfl != nullptr, pack_task(m, I, K, J), t0);
                 if (!ok && threadIdx.x == 0) {
                     if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 3;
                     st_release_s32(&a.ctl->abort, 1);
@@ -238,7 +263,7 @@ struct MixedBody {
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) task_done_bookkeeping(a, type, m, I, K, J, t0);
+        if (threadIdx.x == 0 && !sm.ts.pend) task_done_bookkeeping(a, type, m, I, K, J, t0);
     }
     static __device__ void solve(const Args &, const SchedArgs &, int, Smem &) {}
 };

@@ -149,14 +149,22 @@ enum OpFmt : int32_t { OP_F16 = 0, OP_BF16 = 1, OP_TF32 = 2 };
 struct TcShared {
     uint64_t full[kTcStages];
     uint64_t empty[kTcStages];
-    uint64_t acc_full;
-    uint64_t tmem_empty;
+    uint64_t acc_full[2];   // per accumulator buffer (two when a sub-tile takes <= 256 columns)
+    uint64_t tmem_empty[2];
     uint64_t drain;
     uint32_t tmem_base;
     uint32_t ring;       // stage fills issued (== consumed) before the current task
     uint32_t acc_uses;   // accumulator uses completed before the current task
     uint32_t drains;     // drain barrier completions
     int32_t fail;        // an mbarrier wait expired in this CTA
+    // a single-sub-tile update whose epilogue was deferred (tc_tile_update with
+    // defer_last) to the next call or to tc_flush
+    int32_t pend;
+    uint32_t pend_u;     // its accumulator use
+    float *pend_C;
+    float pend_sa, pend_sb;
+    int32_t pend_nb;
+    uint64_t pend_task, pend_t0;
 };
 
 struct TcGemmArgs {
@@ -174,13 +182,16 @@ __device__ inline void tc_cta_init(TcShared &ts) {
             mbar_init(&ts.full[s], 1);
             mbar_init(&ts.empty[s], 1);
         }
-        mbar_init(&ts.acc_full, 1);
-        mbar_init(&ts.tmem_empty, 4);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ts.acc_full[b], 1);
+            mbar_init(&ts.tmem_empty[b], 4);
+        }
         mbar_init(&ts.drain, 1);
         ts.ring = 0;
         ts.acc_uses = 0;
         ts.drains = 0;
         ts.fail = 0;
+        ts.pend = 0;
         mbar_fence_init();
     }
     if (threadIdx.x / 32 == 1) {
@@ -207,18 +218,106 @@ __device__ inline void tc_cta_fini(TcShared &ts) {
 
 __device__ __forceinline__ int tc_failed(const TcShared &ts) { return *(volatile const int32_t *)&ts.fail; }
 
+// Accumulator use u of a sub-tile of 'cols' tensor-memory columns: buffer and
+// phase.  Sub-tiles of up to 256 columns alternate between two buffers (so
+// the epilogue of one overlaps the MMAs of the next); wider ones use one.
+__device__ __forceinline__ uint32_t tc_buf(uint32_t u, int cols) { return cols <= 256 ? (u & 1) : 0; }
+__device__ __forceinline__ uint32_t tc_phase(uint32_t u, int cols) { return cols <= 256 ? (u >> 1) : u; }
+
+// Epilogue of one sub-tile (rows ri*SR.., columns ci*NN..) from accumulator use
+// u, by the 4 epilogue warps: TMEM -> registers -> shared transpose -> C.  A
+// lane holds one row of a 32 x 32 chunk; the chunk goes through a per-warp
+// shared-memory transpose so that C is read and written row by row with the
+// 32 lanes on 32 consecutive columns (coalesced).  False if a wait expired.
+__device__ inline bool tc_epilogue_sub(TcShared &ts, float *xpose, float *C, int nb, int ri, int ci, float sa,
+                                       float sb, uint32_t u, uint64_t deadline) {
+    const int MH = nb >= 256 ? 2 : 1, NN = nb >= 256 ? 256 : 128, SR = MH * 128, cols = MH * NN;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int q = warp - 4;  // TMEM lane quadrant of this warp
+    float *xp = xpose + q * 32 * 32;
+    const uint32_t b = tc_buf(u, cols), k = tc_phase(u, cols);
+    for (int h = 0; h < MH; ++h) {  // pull this warp's rows of the sub-tile into L2
+        const float *rp = C + (size_t)(ri * SR + h * 128 + q * 32 + lane) * nb + ci * NN;
+        for (int l = 0; l < NN; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + l));
+    }
+    bool got = true;
+    if (lane == 0) got = mbar_wait(&ts.acc_full[b], k & 1, deadline);
+    got = __shfl_sync(0xffffffffu, got, 0);
+    if (!got) return false;
+    tc_fence_after();
+    const uint32_t tcol = b * (uint32_t)cols;
+    for (int h = 0; h < MH; ++h) {
+        const int row0 = ri * SR + h * 128 + q * 32;
+        for (int c = 0; c < NN; c += 32) {
+            uint32_t r[32];
+            tmem_ld32(ts.tmem_base + ((uint32_t)(q * 32) << 16) + tcol + (uint32_t)(h * NN + c), r);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) xp[j * 32 + (lane ^ j)] = (__uint_as_float(r[j]) * sa) * sb;
+            __syncwarp();
+            float *cb = C + (size_t)row0 * nb + ci * NN + c + lane;
+            float cv[32];
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) cv[rr] = __ldcg(cb + (size_t)rr * nb);
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) cb[(size_t)rr * nb] = cv[rr] - xp[lane * 32 + (rr ^ lane)];
+            __syncwarp();
+        }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ts.tmem_empty[b]);
+    return true;
+}
+
+struct TcNoDone {
+    __device__ void operator()(uint64_t, uint64_t) const {}
+};
+
+// The epilogue warps apply a deferred sub-tile, if any, then one thread hands
+// its word to on_done (after all 4 warps' stores: the named barrier).
+template <class Done>
+__device__ inline bool tc_epilogue_pending(TcShared &ts, float *xpose, uint64_t deadline, const Done &on_done) {
+    if (!ts.pend) return true;
+    const bool ok = tc_epilogue_sub(ts, xpose, ts.pend_C, ts.pend_nb, 0, 0, ts.pend_sa, ts.pend_sb, ts.pend_u, deadline);
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // the 4 epilogue warps only
+    if (threadIdx.x == 128 && ok) on_done(ts.pend_task, ts.pend_t0);
+    return ok;
+}
+
+// Apply a deferred sub-tile now (all threads; ends with a barrier).  False if
+// a wait expired.
+template <class Done>
+__device__ inline bool tc_flush(TcShared &ts, float *xpose, uint64_t timeout_ns, const Done &on_done) {
+    bool ok = true;
+    if (threadIdx.x >= 128) ok = tc_epilogue_pending(ts, xpose, global_ns() + timeout_ns, on_done);
+    if (!ok) *(volatile int32_t *)&ts.fail = 1;
+    __syncthreads();
+    ok = !tc_failed(ts);
+    __syncthreads();
+    if (threadIdx.x == 0) ts.pend = 0;
+    __syncthreads();
+    return ok;
+}
+
 // C[nb x nb] -= sa * sb * sum_p A_p B_p^T (sa, sb powers of two, applied one
 // after the other so their product never underflows on its own), A rows
 // starting at row aRow0 of the operand maps, B rows at bRow0.  lower: skip
 // sub-tiles strictly above the diagonal (SYRK).  xpose: 16 KB of shared memory
 // (four 32 x 32 float transpose buffers).  Called by all 256 threads;
-// returns false if a wait expired.
+// returns false if a wait expired.  A deferred sub-tile of the previous call
+// is applied first by the epilogue warps (its completion handed to on_done);
+// with defer_last (tile of order 128: one sub-tile) this call's epilogue is
+// left for the next call or tc_flush, tagged with task / t0.
+template <class Done = TcNoDone>
 __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpose, const TcGemmArgs &g, float *C,
                                       int nb, int aRow0, int bRow0, float sa, float sb, bool lower,
-                                      uint64_t timeout_ns) {
+                                      uint64_t timeout_ns, const Done &on_done = Done(), bool defer_last = false,
+                                      uint64_t task = 0, uint64_t t0 = 0) {
     const int MH = nb >= 256 ? 2 : 1;          // 128-row halves per sub-tile
     const int NN = nb >= 256 ? 256 : 128;      // MMA N
     const int SR = MH * 128;                   // sub-tile rows
+    const int cols = MH * NN;                  // tensor-memory columns of a sub-tile
     const int nsr = nb / SR, nsc = nb / NN;
     const int kchunks = nb / (g.tf32 ? 32 : 64);
     const uint32_t stage_bytes = (uint32_t)(MH + NN / 128) * kBoxBytes;
@@ -231,6 +330,7 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
     for (int ri = 0; ri < nsr; ++ri)
         for (int ci = 0; ci < nsc; ++ci) nsub += skip(ri, ci) ? 0 : 1;
     const uint32_t iters_per_sub = (uint32_t)(g.passes * kchunks);
+    const bool defer = defer_last && nsub == 1 && cols <= 256;
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
@@ -263,11 +363,14 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
         for (int ri = 0; ri < nsr && !tc_failed(ts); ++ri)
             for (int ci = 0; ci < nsc && !tc_failed(ts); ++ci) {
                 if (skip(ri, ci)) continue;
-                if (u > 0 && !mbar_wait(&ts.tmem_empty, (u - 1) & 1, deadline)) {
+                const uint32_t b = tc_buf(u, cols), k = tc_phase(u, cols);
+                // the epilogue of the previous use of this buffer must have read it
+                if (k > 0 && !mbar_wait(&ts.tmem_empty[b], (k - 1) & 1, deadline)) {
                     *(volatile int32_t *)&ts.fail = 1;
                     break;
                 }
                 tc_fence_after();
+                const uint32_t tcol = b * (uint32_t)cols;
                 bool first = true;
                 for (int p = 0; p < g.passes && !tc_failed(ts); ++p)
                     for (int kc = 0; kc < kchunks; ++kc, ++f) {
@@ -283,7 +386,7 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
                             const uint64_t bdesc = sdesc_sw128(base + MH * kBoxBytes + k4 * 32);
                             for (int h = 0; h < MH; ++h) {
                                 const uint64_t adesc = sdesc_sw128(base + h * kBoxBytes + k4 * 32);
-                                const uint32_t d = ts.tmem_base + (uint32_t)(h * NN);
+                                const uint32_t d = ts.tmem_base + tcol + (uint32_t)(h * NN);
                                 if (g.tf32) tc_mma<true>(d, adesc, bdesc, g.idesc, first ? 0u : 1u);
                                 else tc_mma<false>(d, adesc, bdesc, g.idesc, first ? 0u : 1u);
                             }
@@ -291,53 +394,20 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
                         }
                         tc_commit(&ts.empty[s]);
                     }
-                tc_commit(&ts.acc_full);
+                tc_commit(&ts.acc_full[b]);
                 ++u;
             }
     } else if (warp >= 4) {
-        // ---------------- epilogue: TMEM -> registers -> shared transpose -> C
-        // A lane holds one row of a 32 x 32 chunk; the chunk goes through a
-        // per-warp shared-memory transpose so that C is read and written row by
-        // row with the 32 lanes on 32 consecutive columns (coalesced).
-        const int q = warp - 4;  // TMEM lane quadrant of this warp
-        float *xp = xpose + q * 32 * 32;
+        // ---------------- epilogue (a deferred sub-tile of the previous call first)
+        bool ok = tc_epilogue_pending(ts, xpose, deadline, on_done);
         uint32_t u = acc0;
-        for (int ri = 0; ri < nsr; ++ri)
-            for (int ci = 0; ci < nsc; ++ci) {
+        for (int ri = 0; ri < nsr && ok; ++ri)
+            for (int ci = 0; ci < nsc && ok; ++ci) {
                 if (skip(ri, ci)) continue;
-                for (int h = 0; h < MH; ++h) {  // pull this warp's rows of the sub-tile into L2
-                    const float *rp = C + (size_t)(ri * SR + h * 128 + q * 32 + lane) * nb + ci * NN;
-                    for (int l = 0; l < NN; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + l));
-                }
-                if (!mbar_wait(&ts.acc_full, u & 1, deadline)) {
-                    *(volatile int32_t *)&ts.fail = 1;
-                    ri = nsr;
-                    break;
-                }
-                tc_fence_after();
-                for (int h = 0; h < MH; ++h) {
-                    const int row0 = ri * SR + h * 128 + q * 32;
-                    for (int c = 0; c < NN; c += 32) {
-                        uint32_t r[32];
-                        tmem_ld32(ts.tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * NN + c), r);
-                        tmem_ld_wait();
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) xp[j * 32 + (lane ^ j)] = (__uint_as_float(r[j]) * sa) * sb;
-                        __syncwarp();
-                        float *cb = C + (size_t)row0 * nb + ci * NN + c + lane;
-                        float cv[32];
-#pragma unroll
-                        for (int rr = 0; rr < 32; ++rr) cv[rr] = __ldcg(cb + (size_t)rr * nb);
-#pragma unroll
-                        for (int rr = 0; rr < 32; ++rr) cb[(size_t)rr * nb] = cv[rr] - xp[lane * 32 + (rr ^ lane)];
-                        __syncwarp();
-                    }
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&ts.tmem_empty);
+                if (!defer) ok = tc_epilogue_sub(ts, xpose, C, nb, ri, ci, sa, sb, u, deadline);
                 ++u;
             }
+        if (!ok) *(volatile int32_t *)&ts.fail = 1;
     }
     __syncthreads();
     const bool ok = !tc_failed(ts);
@@ -345,6 +415,16 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
     if (threadIdx.x == 0 && ok) {
         ts.ring = ring0 + (uint32_t)nsub * iters_per_sub;
         ts.acc_uses = acc0 + (uint32_t)nsub;
+        ts.pend = defer ? 1 : 0;
+        if (defer) {
+            ts.pend_u = acc0;
+            ts.pend_C = C;
+            ts.pend_sa = sa;
+            ts.pend_sb = sb;
+            ts.pend_nb = nb;
+            ts.pend_task = task;
+            ts.pend_t0 = t0;
+        }
     }
     __syncthreads();
     return ok;
