@@ -61,7 +61,6 @@ struct OzShared {
     int32_t pend;
     uint32_t pend_u;             // its quarter index
     double *pend_C;
-    const int32_t *pend_expA, *pend_expB;
     uint64_t pend_task;          // opaque word handed to the completion callback
     uint64_t pend_t0;
 };
@@ -72,6 +71,7 @@ struct OzSmem {
     uint8_t A[kOzStages][kOzABytes];       // 64 KB
     double xp[kOzEpiWarps][32 * 16];       // 32 KB: per epilogue warp, a 32 x 16 block of C
     int32_t ex[2][kOzNb];                  // column exponents (rows of B): [1] current update, [0] deferred quarter
+    int32_t pea[kOzNb];                    // row exponents (rows of A) of the deferred quarter
     OzShared os;
 };
 
@@ -314,22 +314,27 @@ __device__ inline bool oz_epilogue_quarter(OzSmem &sm, double *C, int qq, uint32
     return true;
 }
 
-// The epilogue warps apply the deferred quarter, if any, then one thread
-// hands its word to on_done (after all 8 warps' stores: the named barrier).
+// The epilogue warps apply the deferred quarter, if any (its exponents were
+// left in shared memory by the call that deferred it: pea, ex[0]).  Its
+// completion is handed to on_done after all 8 warps' stores: with
+// done_by_warp2 the epilogue warps only arrive on named barrier 3 and warp 2
+// (idle in the tile update) waits there and calls on_done, so the epilogue
+// goes on without the completion's round trips; otherwise thread 128 calls
+// it after a barrier of the epilogue warps.
 template <class Done>
-__device__ inline bool oz_epilogue_pending(OzSmem &sm, uint64_t deadline, const Done &on_done) {
+__device__ inline bool oz_epilogue_pending(OzSmem &sm, uint64_t deadline, const Done &on_done, bool done_by_warp2) {
     OzShared &os = sm.os;
     if (!os.pend) return true;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int row = (warp & 3) * 32 + lane;
-    // the deferred quarter's column exponents go to ex[0] (unused otherwise)
-    const int c0 = kOzNb - kOzQ;
-    if (threadIdx.x - 128 < kOzQ) sm.ex[0][c0 + threadIdx.x - 128] = __ldcg(os.pend_expB + c0 + threadIdx.x - 128);
-    asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps only
-    const bool ok = oz_epilogue_quarter(sm, os.pend_C, kOzNb / kOzQ - 1, os.pend_u, __ldcg(os.pend_expA + row),
-                                        sm.ex[0], deadline);
-    asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps only
-    if (warp == 4 && lane == 0 && ok) on_done(os.pend_task, os.pend_t0);
+    const bool ok = oz_epilogue_quarter(sm, os.pend_C, kOzNb / kOzQ - 1, os.pend_u, sm.pea[row], sm.ex[0], deadline);
+    if (!ok) oz_fail(os);
+    if (done_by_warp2) {
+        asm volatile("bar.arrive 3, 288;" ::: "memory");  // 8 epilogue warps + warp 2
+    } else {
+        asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps only
+        if (warp == 4 && lane == 0 && ok) on_done(os.pend_task, os.pend_t0);
+    }
     return ok;
 }
 
@@ -343,7 +348,7 @@ template <class Done>
 __device__ inline bool ozaki_flush(OzSmem &sm, uint64_t timeout_ns, const Done &on_done) {
     OzShared &os = sm.os;
     bool ok = true;
-    if (threadIdx.x >= 128) ok = oz_epilogue_pending(sm, global_ns() + timeout_ns, on_done);
+    if (threadIdx.x >= 128) ok = oz_epilogue_pending(sm, global_ns() + timeout_ns, on_done, false);
     if (!ok) oz_fail(os);
     __syncthreads();
     ok = !oz_failed(os);
@@ -475,14 +480,26 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
         }
         // the previous call's deferred quarter (its accumulators are in the
         // other tensor-memory half than this call's first quarter)
-        bool ok = oz_epilogue_pending(sm, deadline, on_done);
-        for (int i = threadIdx.x - 128; i < kOzNb; i += 32 * kOzEpiWarps) sm.ex[1][i] = __ldcg(expB + i);
         const int ea = __ldcg(expA + row);
+        bool ok = oz_epilogue_pending(sm, deadline, on_done, true);
+        for (int i = threadIdx.x - 128; i < kOzNb; i += 32 * kOzEpiWarps) sm.ex[1][i] = __ldcg(expB + i);
         asm volatile("bar.sync 1, 256;" ::: "memory");  // the 8 epilogue warps only
         const int nq = defer_last ? kQuarters - 1 : kQuarters;
 #pragma unroll 1
         for (int qq = 0; qq < nq && ok; ++qq) ok = oz_epilogue_quarter(sm, C, qq, q0 + qq, ea, sm.ex[1], deadline);
         if (!ok) oz_fail(os);
+        if (defer_last) {
+            // leave the deferred quarter's exponents for the call that applies it
+            if (warp < 8) sm.pea[row] = ea;
+            const int i = (int)threadIdx.x - 128;
+            if (i < kOzQ) sm.ex[0][kOzNb - kOzQ + i] = sm.ex[1][kOzNb - kOzQ + i];
+        }
+    } else if (warp == 2) {
+        // ---------------- completion of the previous call's deferred quarter
+        if (os.pend) {
+            asm volatile("bar.sync 3, 288;" ::: "memory");
+            if (lane == 0 && !oz_failed(os)) on_done(os.pend_task, os.pend_t0);
+        }
     }
     __syncthreads();
     const bool ok = !oz_failed(os);
@@ -494,8 +511,6 @@ __device__ inline bool ozaki_tile_update(OzSmem &sm, const CUtensorMap *mapA, co
         if (defer_last) {
             os.pend_u = q0 + kQuarters - 1;
             os.pend_C = C;
-            os.pend_expA = expA;
-            os.pend_expB = expB;
             os.pend_task = task;
             os.pend_t0 = t0;
         }
