@@ -6,7 +6,8 @@ Each prints one JSON line with the keys of the default FP64 line.
   the SE covariance (n, --nugget, default 1e-2), then a solve of 16 N(0, 1)
   right-hand sides with FP64 iterative refinement to backward error 1e-14.
   value = factorization TFLOP/s (n^3/3); the line also carries the
-  refinement iterations, the backward error, the time to solution and the
+  refinement iterations (with --flags 32, GMRES-based refinement: factor
+  applications), the backward error, the time to solution and the
   plain FP64 path's time to solution (factor + solve) on the same inputs.
   A factorization that breaks down (not positive definite in the chosen
   precision) prints its info instead of a value.
@@ -114,7 +115,8 @@ def run_mixed(args, world, rank, local):
                                             "frac": achieved / peak, "traffic": None,
                                             "kernel": "df_kernel<MixedBody> (whole schedule)",
                                             "peak_source": f"measured bf16 {bf16} TFLOP/s x nominal ratio for {prec}"},
-                               "refinement": {"status": rc, "iterations": iters, "berr": berr,
+                               "refinement": {"method": "gmres" if args.flags & chol.CHOL_FLAG_GMRES_IR else "classic",
+                                              "status": rc, "iterations": iters, "berr": berr,
                                               "solve_s": solve_s, "time_to_solution_s": ms / 1e3 + solve_s},
                                "fp64_reference_path": fp64,
                                "clocks": clk.summary()})

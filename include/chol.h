@@ -90,9 +90,13 @@ enum {
     CHOL_FLAG_GRAPH = 4,         /* fork-join: replay the per-step launches from a cached CUDA graph */
     CHOL_FLAG_TEST_WITHHOLD = 8, /* dataflow test hook: never release the last POTRF, so the
                                     bounded waits must expire with CHOL_ERR_TIMEOUT */
-    CHOL_FLAG_FP64_TC = 16       /* FP64: run SYRK/GEMM on the bf16 tensor cores with binary64
+    CHOL_FLAG_FP64_TC = 16,      /* FP64: run SYRK/GEMM on the bf16 tensor cores with binary64
                                     accuracy (exact 8 x 7-bit slicing of row-scaled values, 36
                                     integer-exact products per update); tiles of order 128 */
+    CHOL_FLAG_GMRES_IR = 32      /* chol_mixed_solve: each refinement step solves the correction
+                                    equation by GMRES(20) preconditioned with the low-precision
+                                    factor (binary64 Krylov vectors) instead of one solve with it;
+                                    iters then counts preconditioner applications */
 };
 
 /* One trace record per executed task (written when opts->trace != NULL). */

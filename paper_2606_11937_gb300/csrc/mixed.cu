@@ -18,6 +18,7 @@
 #include <cuda_fp16.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -361,6 +362,67 @@ __global__ void max_kernel(const double *v, int64_t n, unsigned long long *out) 
     atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
+// ------------------------------------------------------------------ GMRES-based refinement helpers
+// Column-wise operations on n x nrhs column-major FP64 blocks (leading
+// dimension n).  The dot products reduce in a fixed order (per-block partial
+// sums, then one thread per column), so results do not depend on timing.
+constexpr int kDotParts = 128;
+
+__global__ void cols_dot_partial(const double *U, const double *V, int64_t n, double *part) {
+    const int64_t c = blockIdx.y, chunk = (n + kDotParts - 1) / kDotParts;
+    const int64_t i0 = blockIdx.x * chunk, i1 = i0 + chunk < n ? i0 + chunk : n;
+    double s = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(U[c * n + i], V[c * n + i], s);
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[c * kDotParts + blockIdx.x] = red[0];
+}
+
+// out[c] = sum of the partials (sqrt of it with take_sqrt)
+__global__ void cols_dot_final(const double *part, int64_t nrhs, double *out, int take_sqrt) {
+    const int64_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nrhs) return;
+    double s = 0.0;
+    for (int b = 0; b < kDotParts; ++b) s += part[c * kDotParts + b];
+    out[c] = take_sqrt ? sqrt(s) : s;
+}
+
+// W[:, c] += sgn * coef[c] * V[:, c]
+__global__ void cols_axpy(double *W, const double *V, const double *coef, double sgn, int64_t n, int64_t nrhs) {
+    const int64_t c = blockIdx.y;
+    const double a = sgn * coef[c];
+    for (int64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        W[c * n + i] = fma(a, V[c * n + i], W[c * n + i]);
+}
+
+// X[:, c] += coef[c] * V[:, c] for X with leading dimension ldx
+__global__ void cols_axpy_ld(double *X, int64_t ldx, const double *V, const double *coef, int64_t n, int64_t nrhs) {
+    const int64_t c = blockIdx.y;
+    const double a = coef[c];
+    for (int64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        X[c * ldx + i] = fma(a, V[c * n + i], X[c * ldx + i]);
+}
+
+// V[:, c] = V[:, c] / nrm[c] (zero column when nrm[c] == 0)
+__global__ void cols_normalize(double *V, const double *nrm, int64_t n, int64_t nrhs) {
+    const int64_t c = blockIdx.y;
+    const double r = nrm[c] > 0.0 ? 1.0 / nrm[c] : 0.0;
+    for (int64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        V[c * n + i] *= r;
+}
+
+// W = sgn * (double)D (binary32 solve result back to binary64)
+__global__ void f32_to_f64_kernel(const float *D, double *W, double sgn, int64_t n, int64_t nrhs) {
+    const int64_t c = blockIdx.y;
+    for (int64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        W[c * n + i] = sgn * (double)D[c * n + i];
+}
+
 }  // namespace chol
 
 // ------------------------------------------------------------------ handle
@@ -499,6 +561,113 @@ static int mixed_factor_impl(int64_t n, const double *A, int64_t lda, const chol
     return rc;
 }
 
+// ------------------------------------------------------------------ GMRES-based refinement
+// One correction X += d with d ~ A^{-1} R, by GMRES(m) on the left-
+// preconditioned system M^{-1} A d = M^{-1} R, M = L^ L^T the binary32 factor
+// (Carson and Higham's GMRES-IR): Arnoldi with modified Gram-Schmidt in
+// binary64, A v in binary64, M^{-1} by the binary32 triangular solves, Givens
+// rotations per right-hand side on the host.  The inner iteration stops when
+// every column's preconditioned residual has dropped by rtol, or after m
+// steps.  *napply counts the preconditioner applications.
+struct GmresWs {
+    double *V;      // (m + 1) blocks of n x nrhs
+    double *zero;   // n x nrhs zeros (right-hand side of the A v product)
+    double *U;      // n x nrhs
+    float *D;       // n x nrhs, binary32 solves
+    double *part;   // nrhs x kDotParts partial dot products
+    double *hcol;   // (m + 2) x nrhs Hessenberg column / coefficients
+    void *sws;      // solve workspace
+};
+
+constexpr int kGmresMaxM = 32;
+
+static int gmres_correction(chol_factor_s *h, const double *R, double *X, int64_t ldx, int64_t nrhs, const GmresWs &w,
+                            cudaStream_t st, int m, double rtol, int *napply) {
+    const int64_t n = h->n;
+    const chol_opts &o = h->opts;
+    if (m > kGmresMaxM) m = kGmresMaxM;
+    const int nblk = (int)((n + kSB - 1) / kSB), ny = (int)((nrhs + kRC - 1) / kRC);
+    const unsigned gx = (unsigned)((n + 255) / 256 < 512 ? (n + 255) / 256 : 512);
+    const dim3 vg(gx, (unsigned)nrhs), vgrid((unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), (unsigned)nrhs);
+    const size_t blk = (size_t)n * nrhs;
+    int rc = CHOL_OK;
+    auto precond = [&](const double *Y, double *Out, double sgn) {
+        to_f32_kernel<<<vgrid, 256, 0, st>>>(Y, n, w.D, n, nrhs);
+        rc = launch_solve<float, TileMajorL<float>>(TileMajorL<float>{h->store, h->nb}, w.D, n, n, nrhs, w.sws,
+                                                    o.timeout_s, st);
+        f32_to_f64_kernel<<<vg, 256, 0, st>>>(w.D, Out, sgn, n, nrhs);
+        ++*napply;
+    };
+    auto dot = [&](const double *Ap, const double *Bp, double *out, int take_sqrt) {
+        cols_dot_partial<<<dim3(kDotParts, (unsigned)nrhs), 256, 0, st>>>(Ap, Bp, n, w.part);
+        cols_dot_final<<<(unsigned)((nrhs + 127) / 128), 128, 0, st>>>(w.part, nrhs, out, take_sqrt);
+    };
+    std::vector<double> hc((size_t)(m + 2) * nrhs), beta(nrhs), g((size_t)(m + 1) * nrhs, 0.0);
+    std::vector<double> Rm((size_t)(m + 1) * m * nrhs, 0.0), cs((size_t)m * nrhs), sn((size_t)m * nrhs);
+    // v0 = M^{-1} r / ||M^{-1} r||
+    precond(R, w.V, 1.0);
+    if (rc != CHOL_OK) return rc;
+    dot(w.V, w.V, w.hcol, 1);
+    cols_normalize<<<vg, 256, 0, st>>>(w.V, w.hcol, n, nrhs);
+    CHOL_CUDA(cudaMemcpyAsync(beta.data(), w.hcol, nrhs * 8, cudaMemcpyDeviceToHost, st));
+    CHOL_CUDA(cudaStreamSynchronize(st));
+    for (int64_t c = 0; c < nrhs; ++c) g[c] = beta[c];
+    int kend = -1;
+    for (int k = 0; k < m; ++k) {
+        double *Vk = w.V + (size_t)k * blk, *Vk1 = w.V + (size_t)(k + 1) * blk;
+        // Vk1 = M^{-1} A Vk (the residual kernel gives U = 0 - A Vk)
+        residual_kernel<<<dim3(nblk, ny), 256, 0, st>>>(h->A, h->lda, n, Vk, n, w.zero, n, w.U, n, nrhs);
+        precond(w.U, Vk1, -1.0);
+        if (rc != CHOL_OK) return rc;
+        for (int j = 0; j <= k; ++j) {
+            dot(Vk1, w.V + (size_t)j * blk, w.hcol + (size_t)j * nrhs, 0);
+            cols_axpy<<<vg, 256, 0, st>>>(Vk1, w.V + (size_t)j * blk, w.hcol + (size_t)j * nrhs, -1.0, n, nrhs);
+        }
+        dot(Vk1, Vk1, w.hcol + (size_t)(k + 1) * nrhs, 1);
+        cols_normalize<<<vg, 256, 0, st>>>(Vk1, w.hcol + (size_t)(k + 1) * nrhs, n, nrhs);
+        CHOL_CUDA(cudaMemcpyAsync(hc.data(), w.hcol, (size_t)(k + 2) * nrhs * 8, cudaMemcpyDeviceToHost, st));
+        CHOL_CUDA(cudaStreamSynchronize(st));
+        double worst = 0.0;
+        for (int64_t c = 0; c < nrhs; ++c) {
+            double col[kGmresMaxM + 1];
+            for (int j = 0; j <= k + 1; ++j) col[j] = hc[(size_t)j * nrhs + c];
+            for (int j = 0; j < k; ++j) {  // previous rotations
+                const double a = col[j], b = col[j + 1];
+                col[j] = cs[j * nrhs + c] * a + sn[j * nrhs + c] * b;
+                col[j + 1] = -sn[j * nrhs + c] * a + cs[j * nrhs + c] * b;
+            }
+            const double a = col[k], b = col[k + 1], r = hypot(a, b);
+            const double cc = r > 0.0 ? a / r : 1.0, ss = r > 0.0 ? b / r : 0.0;
+            cs[k * nrhs + c] = cc;
+            sn[k * nrhs + c] = ss;
+            col[k] = r;
+            col[k + 1] = 0.0;
+            for (int j = 0; j <= k; ++j) Rm[((size_t)j * m + k) * nrhs + c] = col[j];
+            const double gk = g[(size_t)k * nrhs + c];
+            g[(size_t)k * nrhs + c] = cc * gk;
+            g[(size_t)(k + 1) * nrhs + c] = -ss * gk;
+            const double rel = beta[c] > 0.0 ? fabs(g[(size_t)(k + 1) * nrhs + c]) / beta[c] : 0.0;
+            worst = rel > worst ? rel : worst;
+        }
+        kend = k;
+        if (!(worst > rtol)) break;  // also stops on a NaN
+    }
+    // y = R^{-1} g per column, X += sum_j y_j v_j
+    std::vector<double> y((size_t)(kend + 1) * nrhs, 0.0);
+    for (int64_t c = 0; c < nrhs; ++c)
+        for (int j = kend; j >= 0; --j) {
+            double v = g[(size_t)j * nrhs + c];
+            for (int l = j + 1; l <= kend; ++l) v -= Rm[((size_t)j * m + l) * nrhs + c] * y[(size_t)l * nrhs + c];
+            const double d = Rm[((size_t)j * m + j) * nrhs + c];
+            y[(size_t)j * nrhs + c] = d != 0.0 ? v / d : 0.0;
+        }
+    CHOL_CUDA(cudaMemcpyAsync(w.hcol, y.data(), y.size() * 8, cudaMemcpyHostToDevice, st));
+    for (int j = 0; j <= kend; ++j)
+        cols_axpy_ld<<<vg, 256, 0, st>>>(X, ldx, w.V + (size_t)j * blk, w.hcol + (size_t)j * nrhs, n, nrhs);
+    CHOL_CUDA(cudaStreamSynchronize(st));  // y lives on the host stack
+    return rc;
+}
+
 static thread_local chol_stats g_mixed_stats;
 
 extern "C" {
@@ -564,14 +733,39 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
     const size_t b_r = a256((size_t)n * nrhs * 8), b_d = a256((size_t)n * nrhs * 4);
     const size_t b_max = a256((size_t)3 * nrhs * 8 + 8), b_rows = a256((size_t)n * 8);
     const size_t b_sws = a256(solve_ws_bytes(n, nrhs));
+    const bool gmres = (o.flags & CHOL_FLAG_GMRES_IR) != 0;
+    // GMRES(20); the inner iteration stops once the preconditioned residual has
+    // dropped by max(1e-6, 0.1 tol / berr): below about 1e-6 the binary32
+    // rounding of the preconditioner's input limits what one correction can
+    // gain, and near the target a smaller reduction suffices.
+    constexpr int kGmresM = 20;
+    const size_t b_g = gmres ? (size_t)(kGmresM + 3) * b_r + a256((size_t)nrhs * kDotParts * 8) +
+                                   a256((size_t)(kGmresM + 2) * nrhs * 8)
+                             : 0;
     void *ws = nullptr;
-    CHOL_CUDA(cudaMallocAsync(&ws, b_r + b_d + b_max + b_rows + b_sws, st));
+    CHOL_CUDA(cudaMallocAsync(&ws, b_r + b_d + b_max + b_rows + b_sws + b_g, st));
     char *p = (char *)ws;
     double *R = (double *)p;
     float *D = (float *)(p + b_r);
     unsigned long long *mx = (unsigned long long *)(p + b_r + b_d);
     double *rows = (double *)(p + b_r + b_d + b_max);
     void *sws = p + b_r + b_d + b_max + b_rows;
+    GmresWs gw{};
+    if (gmres) {
+        char *q = p + b_r + b_d + b_max + b_rows + b_sws;
+        gw.V = (double *)q;
+        q += (size_t)(kGmresM + 1) * b_r;
+        gw.zero = (double *)q;
+        q += b_r;
+        gw.U = (double *)q;
+        q += b_r;
+        gw.part = (double *)q;
+        q += a256((size_t)nrhs * kDotParts * 8);
+        gw.hcol = (double *)q;
+        gw.D = D;
+        gw.sws = sws;
+    }
+    int napply = 0;
     const int nblk = (int)((n + kSB - 1) / kSB), ny = (int)((nrhs + kRC - 1) / kRC);
     const dim3 vgrid((unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), (unsigned)nrhs);
     int rc = CHOL_OK;
@@ -591,7 +785,8 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
             }
             memcpy(&h->anorm, &v, 8);
         }
-        if (cudaMemset2DAsync(X, ldx * 8, 0, n * 8, nrhs, st) != cudaSuccess) {
+        if (cudaMemset2DAsync(X, ldx * 8, 0, n * 8, nrhs, st) != cudaSuccess ||
+            (gmres && cudaMemsetAsync(gw.zero, 0, b_r, st) != cudaSuccess)) {
             rc = cuda_fail(cudaGetLastError(), "zero X", __FILE__, __LINE__);
             break;
         }
@@ -627,6 +822,12 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
             }
             if (!finite) berr = __builtin_nan("");
             if (berr <= o.refine_tol || it >= o.max_iter || !(berr == berr)) break;
+            if (gmres) {
+                const double rt = std::min(0.5, std::max(1e-6, 0.1 * o.refine_tol / berr));
+                rc = gmres_correction(h, R, X, ldx, nrhs, gw, st, kGmresM, rt, &napply);
+                if (rc != CHOL_OK) break;
+                continue;
+            }
             // d = L^-T L^-1 r in binary32 on the tile store; x += d
             to_f32_kernel<<<vgrid, 256, 0, st>>>(R, n, D, n, nrhs);
             rc = launch_solve<float, TileMajorL<float>>(TileMajorL<float>{h->store, h->nb}, D, n, n, nrhs, sws,
@@ -645,7 +846,7 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
         }
     } while (0);
     cudaFreeAsync(ws, st);
-    if (iters_out) *iters_out = it;
+    if (iters_out) *iters_out = gmres ? napply : it;
     if (berr_out) *berr_out = berr;
     if (rc == CHOL_OK && !(berr <= o.refine_tol)) {
         set_error("refinement stopped at backward error %.3e after %d iterations", berr, it);

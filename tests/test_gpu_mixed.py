@@ -117,6 +117,39 @@ def test_refinement_status_on_harder_input():
         h.close()
 
 
+@pytest.mark.parametrize("prec", ["tf32", "fp16"])
+@pytest.mark.parametrize("nugget", [1e-1, 1e-2])
+def test_gmres_refinement(prec, nugget):
+    """CHOL_FLAG_GMRES_IR: each correction by GMRES preconditioned with the
+    low-precision factor.  Where the factor exists, the solve reaches the
+    FP64 backward error 1e-14 (checked by the oracle) and matches the oracle's
+    solution, also where classic refinement stalls."""
+    import torch
+
+    import paper_2606_11937_gb300 as chol
+    n = 1536
+    A = matrix("se", n, 1, nugget)
+    B = si.rhs(n, 3, seed=6)
+    rc, h, dA = mixed(A, prec, "dataflow", 128, max_iter=40, flags=chol.CHOL_FLAG_GMRES_IR)
+    if rc != 0 or h.info != 0:
+        pytest.skip(f"{prec} factor breaks down at nugget {nugget} (info {h.info})")
+    rc, dX, napply, berr = h.solve(chol.colmajor(B), raise_on_error=False)
+    torch.cuda.synchronize()
+    X = dX.cpu().numpy()
+    be = oracle.backward_error(A, X, B)
+    h.close()
+    rc2, h2, _ = mixed(A, prec, "dataflow", 128, max_iter=40)
+    rc2, _, iters, berr2 = h2.solve(chol.colmajor(B), raise_on_error=False)
+    h2.close()
+    print(f"{prec} nugget {nugget}: GMRES rc {rc} applications {napply} berr {berr:.2e} oracle {be:.2e}; "
+          f"classic rc {rc2} iterations {iters} berr {berr2:.2e}")
+    assert rc == 0 and berr <= 1e-14 and be <= 1e-14
+    Lref, _ = oracle_factor("se", n, 1, nugget)
+    Xref = oracle.potrs(Lref, B)
+    kappa_u = 1e-16 * np.linalg.cond(A, 1)
+    assert np.max(np.abs(X - Xref)) <= max(1e-12, 10 * kappa_u) * np.max(np.abs(Xref))
+
+
 def test_mixed_non_spd_info():
     n = 1024
     A = matrix("gram", n, 4).copy()
