@@ -37,6 +37,16 @@ int chol_test_tc_update(int32_t precision, int64_t nb, const void *ops, int32_t 
  * CHOL_ERR_CUDA or CHOL_ERR_TIMEOUT. */
 int chol_test_ozaki_update(const double *A, const double *B, double *C);
 
+/* The refinement residual on the tensor cores alone: R = B - A X (B may be
+ * NULL: R = -A X) with binary64 accuracy from exact bf16 slicing of A (every
+ * 128 x 128 tile, rows scaled per tile) and X (per 128-row block and column).
+ * A: n x n symmetric, only its lower triangle is read (column-major, lda);
+ * X, B, R: n x nrhs column-major; all device pointers.  Allocates and frees
+ * its own scratch (about n^2 / 2 bytes x 8 for the slices).  Returns CHOL_OK,
+ * CHOL_ERR_ARG, CHOL_ERR_CUDA or CHOL_ERR_TIMEOUT. */
+int chol_test_oz_residual(int64_t n, const double *A, int64_t lda, const double *X, int64_t ldx,
+                          const double *B, int64_t ldb, double *R, int64_t ldr, int64_t nrhs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // 2-D map over `rows` rows of nb elements (row pitch nb * elem bytes), boxes of
 // 128 bytes of K x box_rows rows, 128-byte swizzle.
+size_t ozr_a_bytes(int64_t n);
+bool ozr_supported(int64_t n);
+int ozr_prepare_a(const double *A, int64_t lda, int64_t n, void *abuf, cudaStream_t st);
+size_t ozr_ws_bytes(int64_t n, int64_t nrhs, int num_ctas);
+int ozr_residual(const void *abuf, int64_t n, const double *X, int64_t ldx, const double *B, int64_t ldb, double *R,
+                 int64_t ldr, int64_t nrhs, void *ws, double timeout_s, cudaStream_t st);
+
 int make_operand_map(CUtensorMap *map, void *base, int fmt, int64_t rows, int64_t nb, int box_rows) {
     auto enc = tensor_map_encoder();
     if (!enc) {
@@ -434,7 +441,35 @@ struct chol_factor_s {
     chol_opts opts{};
     double anorm = -1.0;        // ||A||_inf, computed on first solve
     int64_t info = 0;           // factorization info (> 0: broke down at that column)
+    void *ozr_a = nullptr;      // slices of A for the tensor-core residual (built on first solve)
+    bool ozr_tried = false;
 };
+
+// order from which the refinement residual runs on the tensor cores
+constexpr int64_t kOzrMinN = 1024;
+
+namespace chol {
+
+// Residual R = B - A X of the refinement (B null: R = -A X): on the tensor
+// cores with binary64 accuracy (ozres.cu) when the handle holds the slices of
+// A, else by the binary64 CUDA-core kernel (zero: an n x nrhs zero block for
+// its B operand).
+struct ResidualOp {
+    chol_factor_s *h;
+    void *ozws;
+    const double *zero;
+    cudaStream_t st;
+    int operator()(const double *X, int64_t ldx, const double *B, int64_t ldb, double *R, int64_t nrhs) const {
+        const int64_t n = h->n;
+        if (h->ozr_a) return ozr_residual(h->ozr_a, n, X, ldx, B, ldb, R, n, nrhs, ozws, h->opts.timeout_s, st);
+        const int nblk = (int)((n + kSB - 1) / kSB), ny = (int)((nrhs + kRC - 1) / kRC);
+        residual_kernel<<<dim3(nblk, ny), 256, 0, st>>>(h->A, h->lda, n, X, ldx, B ? B : zero, B ? ldb : n, R, n,
+                                                         nrhs);
+        return CHOL_OK;
+    }
+};
+
+}  // namespace chol
 
 using namespace chol;
 
@@ -582,7 +617,7 @@ struct GmresWs {
 constexpr int kGmresMaxM = 32;
 
 static int gmres_correction(chol_factor_s *h, const double *R, double *X, int64_t ldx, int64_t nrhs, const GmresWs &w,
-                            cudaStream_t st, int m, double rtol, int *napply) {
+                            const ResidualOp &resid, cudaStream_t st, int m, double rtol, int *napply) {
     const int64_t n = h->n;
     const chol_opts &o = h->opts;
     if (m > kGmresMaxM) m = kGmresMaxM;
@@ -616,7 +651,8 @@ static int gmres_correction(chol_factor_s *h, const double *R, double *X, int64_
     for (int k = 0; k < m; ++k) {
         double *Vk = w.V + (size_t)k * blk, *Vk1 = w.V + (size_t)(k + 1) * blk;
         // Vk1 = M^{-1} A Vk (the residual kernel gives U = 0 - A Vk)
-        residual_kernel<<<dim3(nblk, ny), 256, 0, st>>>(h->A, h->lda, n, Vk, n, w.zero, n, w.U, n, nrhs);
+        rc = resid(Vk, n, nullptr, n, w.U, nrhs);
+        if (rc != CHOL_OK) return rc;
         precond(w.U, Vk1, -1.0);
         if (rc != CHOL_OK) return rc;
         for (int j = 0; j <= k; ++j) {
@@ -730,6 +766,23 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
     const chol_opts &o = h->opts;
     cudaStream_t st = (cudaStream_t)o.stream;
     prepare_pool();
+    if (!h->ozr_tried) {
+        // slices of A for the tensor-core residual, once per handle (A stays
+        // unchanged while the handle lives); without the memory for them the
+        // binary64 CUDA-core residual is used
+        h->ozr_tried = true;
+        if (n >= kOzrMinN && ozr_supported(n)) {
+            if (cudaMallocAsync(&h->ozr_a, ozr_a_bytes(n), st) != cudaSuccess) {
+                cudaGetLastError();
+                h->ozr_a = nullptr;
+            } else if (ozr_prepare_a(h->A, h->lda, n, h->ozr_a, st) != CHOL_OK) {
+                cudaFreeAsync(h->ozr_a, st);
+                h->ozr_a = nullptr;
+                cudaGetLastError();
+            }
+        }
+    }
+    const size_t b_oz = h->ozr_a ? a256(ozr_ws_bytes(n, nrhs, num_sms())) : 0;
     const size_t b_r = a256((size_t)n * nrhs * 8), b_d = a256((size_t)n * nrhs * 4);
     const size_t b_max = a256((size_t)3 * nrhs * 8 + 8), b_rows = a256((size_t)n * 8);
     const size_t b_sws = a256(solve_ws_bytes(n, nrhs));
@@ -743,7 +796,7 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
                                    a256((size_t)(kGmresM + 2) * nrhs * 8)
                              : 0;
     void *ws = nullptr;
-    CHOL_CUDA(cudaMallocAsync(&ws, b_r + b_d + b_max + b_rows + b_sws + b_g, st));
+    CHOL_CUDA(cudaMallocAsync(&ws, b_r + b_d + b_max + b_rows + b_sws + b_g + b_oz, st));
     char *p = (char *)ws;
     double *R = (double *)p;
     float *D = (float *)(p + b_r);
@@ -765,6 +818,8 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
         gw.D = D;
         gw.sws = sws;
     }
+    void *ozws = b_oz ? (void *)(p + b_r + b_d + b_max + b_rows + b_sws + b_g) : nullptr;
+    const ResidualOp resid{h, ozws, gw.zero, st};
     int napply = 0;
     const int nblk = (int)((n + kSB - 1) / kSB), ny = (int)((nrhs + kRC - 1) / kRC);
     const dim3 vgrid((unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), (unsigned)nrhs);
@@ -799,7 +854,8 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
                     break;
                 }
             } else {
-                residual_kernel<<<dim3(nblk, ny), 256, 0, st>>>(h->A, h->lda, n, X, ldx, B, ldb, R, n, nrhs);
+                rc = resid(X, ldx, B, ldb, R, nrhs);
+                if (rc != CHOL_OK) break;
             }
             if (cudaMemsetAsync(mx, 0, 3 * nrhs * 8, st) != cudaSuccess) { rc = CHOL_ERR_CUDA; break; }
             colmax_kernel<<<vgrid, 256, 0, st>>>(R, n, X, ldx, B, ldb, n, nrhs, mx);
@@ -824,7 +880,7 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
             if (berr <= o.refine_tol || it >= o.max_iter || !(berr == berr)) break;
             if (gmres) {
                 const double rt = std::min(0.5, std::max(1e-6, 0.1 * o.refine_tol / berr));
-                rc = gmres_correction(h, R, X, ldx, nrhs, gw, st, kGmresM, rt, &napply);
+                rc = gmres_correction(h, R, X, ldx, nrhs, gw, resid, st, kGmresM, rt, &napply);
                 if (rc != CHOL_OK) break;
                 continue;
             }
@@ -837,11 +893,12 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
         }
         if (rc == CHOL_OK && cudaGetLastError() != cudaSuccess) rc = CHOL_ERR_CUDA;
         if (rc == CHOL_OK) {
-            int32_t sst = 0;
+            int32_t sst = 0, ost = 0;
             if (cudaMemcpyAsync(&sst, sws, 4, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
-                cudaStreamSynchronize(st) == cudaSuccess && sst != 0) {
-                set_error("refinement solve: device-side wait expired");
-                rc = sst;
+                (!ozws || cudaMemcpyAsync(&ost, ozws, 4, cudaMemcpyDeviceToHost, st) == cudaSuccess) &&
+                cudaStreamSynchronize(st) == cudaSuccess && (sst != 0 || ost != 0)) {
+                set_error("refinement %s: device-side wait expired", sst ? "solve" : "residual");
+                rc = sst ? sst : ost;
             }
         }
     } while (0);
@@ -858,7 +915,9 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
 void chol_factor_free(chol_factor_h h) {
     if (!h) return;
     if (h->store) cudaFreeAsync(h->store, (cudaStream_t)h->opts.stream);
+    if (h->ozr_a) cudaFreeAsync(h->ozr_a, (cudaStream_t)h->opts.stream);
     h->store = nullptr;
+    h->ozr_a = nullptr;
     delete h;
 }
 

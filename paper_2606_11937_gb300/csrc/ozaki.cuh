@@ -91,54 +91,64 @@ __device__ __forceinline__ uint16_t small_int_bf16(uint32_t a, uint32_t neg) {
     return (uint16_t)((neg << 15) | ((127u + msb) << 7) | mant);
 }
 
+// Split one row of 128 binary64 values (v[q] is column lane + 32 q; one
+// warp) into 8 bf16 slices and return the row exponent e (|row| < 2^e).
+// With x = v 2^-e in (-1, 1) and X = floor(|x| 2^56), slice s (1-based) is
+// sign(x) times bits [56 - 7s, 63 - 7s) of X -- the digits the recursion
+// t = 128 x, a = trunc(t), x = t - a produces -- computed with integer
+// operations on the binary64 encoding.  Slice s (0-based) of column c goes
+// to o[s * sstride + c]; `negate` splits -v.
+__device__ __forceinline__ int ozaki_split_row(const double (&v)[4], uint16_t *o, size_t sstride, bool negate) {
+    const int lane = threadIdx.x % 32;
+    double m = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) m = fmax(m, fabs(v[q]));
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    int e = 0;
+    if (m > 0.0 && isfinite(m)) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |row| < 2^e
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(v[q]);
+        const uint32_t neg = (uint32_t)(bits >> 63) ^ (negate ? 1u : 0u);
+        const int expo = (int)((bits >> 52) & 0x7FF);
+        unsigned long long M = bits & ((1ull << 52) - 1);
+        int qexp;                      // |v| = M 2^qexp
+        if (expo == 0) qexp = -1074;   // subnormal or zero
+        else {
+            M |= 1ull << 52;
+            qexp = expo - 1075;
+        }
+        const int sh = qexp - e + 56;  // X = floor(M 2^sh) < 2^56
+        unsigned long long X;
+        if (sh >= 0) X = M << sh;
+        else X = sh <= -64 ? 0ull : (M >> (-sh));
+        uint16_t *oc = o + lane + 32 * q;
+#pragma unroll
+        for (int s = 0; s < kOzS; ++s) {
+            const uint32_t a = (uint32_t)((X >> (49 - 7 * s)) & 127u);
+            oc[(size_t)s * sstride] = small_int_bf16(a, neg);
+        }
+    }
+    return e;
+}
+
 // Split a 128 x 128 binary64 tile into 8 bf16 slices ([s][r][c], 32 KB each)
-// and one exponent per row.  With x = v 2^-e in (-1, 1) and
-// X = floor(|x| 2^56), slice s (1-based) is sign(x) times bits
-// [56 - 7s, 63 - 7s) of X -- the digits the recursion t = 128 x,
-// a = trunc(t), x = t - a produces -- computed with integer operations on
-// the binary64 encoding.  Element (r, c) is T[r * 128 + c], or T[c * 128 + r]
-// with `transpose`; `negate` splits -T.  All threads of the CTA; ends with a
-// barrier.
+// and one exponent per row (ozaki_split_row per row).  Element (r, c) is
+// T[r * 128 + c], or T[c * 128 + r] with `transpose`; `negate` splits -T.
+// All threads of the CTA; ends with a barrier.
 __device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32_t *rexp, bool negate = false,
                                    bool transpose = false) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
     uint16_t *out = reinterpret_cast<uint16_t *>(slices);
     for (int r = warp; r < kOzNb; r += nwarps) {
         double v[4];
-        double m = 0.0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int c = lane + 32 * q;
             v[q] = __ldcg(T + (transpose ? (size_t)c * kOzNb + r : (size_t)r * kOzNb + c));
-            m = fmax(m, fabs(v[q]));
         }
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        int e = 0;
-        if (m > 0.0 && isfinite(m)) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |row| < 2^e
+        const int e = ozaki_split_row(v, out + (size_t)r * kOzNb, (size_t)kOzNb * kOzNb, negate);
         if (lane == 0) rexp[r] = e;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(v[q]);
-            const uint32_t neg = (uint32_t)(bits >> 63) ^ (negate ? 1u : 0u);
-            const int expo = (int)((bits >> 52) & 0x7FF);
-            unsigned long long M = bits & ((1ull << 52) - 1);
-            int qexp;                      // |v| = M 2^qexp
-            if (expo == 0) qexp = -1074;   // subnormal or zero
-            else {
-                M |= 1ull << 52;
-                qexp = expo - 1075;
-            }
-            const int sh = qexp - e + 56;  // X = floor(M 2^sh) < 2^56
-            unsigned long long X;
-            if (sh >= 0) X = M << sh;
-            else X = sh <= -64 ? 0ull : (M >> (-sh));
-            uint16_t *o = out + (size_t)r * kOzNb + lane + 32 * q;
-#pragma unroll
-            for (int s = 0; s < kOzS; ++s) {
-                const uint32_t a = (uint32_t)((X >> (49 - 7 * s)) & 127u);
-                o[(size_t)s * kOzNb * kOzNb] = small_int_bf16(a, neg);
-            }
-        }
     }
     fence_proxy_async_global();
     __syncthreads();

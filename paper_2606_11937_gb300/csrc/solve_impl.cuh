@@ -1,11 +1,14 @@
 // solve_impl.cuh -- triangular solves with the Cholesky factor:
 // forward substitution L Y = B, then backward substitution L^T X = Y.
 //
-// Each sweep is one persistent "wavefront" launch over row blocks of 64.  A
-// CTA takes a ticket (atomic counter), which fixes the block it solves in
-// ticket order, so it only ever waits for blocks owned by CTAs that started
-// before it (no deadlock whatever the residency).  It accumulates the
-// contributions of the finished blocks as their ready flags appear (acquire),
+// Each sweep is one "wavefront" launch over row blocks of 64.  A CTA takes a
+// ticket (atomic counter), which fixes the block it solves in ticket order,
+// so it only ever waits for blocks owned by CTAs that started before it (no
+// deadlock whatever the residency).  It accumulates the contributions of the
+// finished blocks in order as their ready flags appear (acquire): the next
+// factor block is loaded into registers while the current one is applied, and
+// one flag poll also takes note of the further blocks that are already
+// finished, whose solution values are then prefetched the same way.  It then
 // solves its diagonal block (loaded before the waits; one warp per pair of
 // right-hand sides, shuffles instead of block barriers), stores the result
 // and releases its own flag.
@@ -22,12 +25,23 @@ constexpr int kSB = 64;  // row block of the solve
 constexpr int kRC = 16;  // right-hand-side columns per CTA
 
 // Factor accessors: element (i, j), i >= j, of L.
+// block(r0, c0) gives the address of element (r0, c0) of a 64 x 64 block that
+// lies in one contiguous piece of storage (valid when blocked() is true): element
+// (r0 + r, c0 + c) is at p + r * rs + c * cs.
+template <typename T>
+struct BlockRef {
+    const T *p;
+    int64_t rs, cs;
+};
+
 template <typename T>
 struct ColMajorL {
     const T *p;
     int64_t ld;
     static constexpr bool kRowsFastest = true;  // consecutive i are contiguous
     __device__ __forceinline__ T operator()(int64_t i, int64_t j) const { return __ldcg(p + j * ld + i); }
+    __device__ __forceinline__ bool blocked() const { return true; }
+    __device__ __forceinline__ BlockRef<T> block(int64_t r0, int64_t c0) const { return {p + c0 * ld + r0, 1, ld}; }
 };
 
 template <typename T>
@@ -38,6 +52,12 @@ struct TileMajorL {
     __device__ __forceinline__ T operator()(int64_t i, int64_t j) const {
         const int64_t I = i / nb, K = j / nb;
         return __ldcg(p + (size_t)tile_index(I, K) * nb * nb + (i - I * nb) * nb + (j - K * nb));
+    }
+    // a 64 x 64 block at a multiple of 64 stays inside one tile when 64 divides nb
+    __device__ __forceinline__ bool blocked() const { return nb % 64 == 0; }
+    __device__ __forceinline__ BlockRef<T> block(int64_t r0, int64_t c0) const {
+        const int64_t I = r0 / nb, K = c0 / nb;
+        return {p + (size_t)tile_index(I, K) * nb * nb + (r0 - I * nb) * nb + (c0 - K * nb), nb, 1};
     }
 };
 
@@ -54,28 +74,58 @@ struct SolveSmem {
     T rinv[kSB];          // reciprocals of its diagonal
     T Xs[kSB][kRC + 1];
     int I;
+    int known;            // leading blocks of the sweep known to be finished
 };
 
-// Load the diagonal block (rows and columns [r0, r0+64)) into Ld and the
-// reciprocals of its diagonal into rinv; ends with a barrier.
-template <typename T, class Acc>
-__device__ void load_diag(const Acc &L, int64_t n, int64_t r0, SolveSmem<T> &sm) {
-    for (int e = threadIdx.x; e < kSB * kSB; e += blockDim.x) {
-        int r, c;
-        if (Acc::kRowsFastest) { r = e % kSB; c = e / kSB; }
-        else { r = e / kSB; c = e % kSB; }
-        const int64_t i = r0 + r, j = r0 + c;
-        T v = T(0);
-        if (i < n && j < n) {
-            if (j <= i) v = L(i, j);
-        } else if (i == j) {
-            v = T(1);
-        }
-        sm.Ld[r][c] = v;
+// Register share of one 64 x 64 block: thread t holds 16 elements, (r, c)
+// with r = t % 64, c = t / 64 + 4 q when consecutive rows are contiguous in
+// memory, else r = t / 64 + 4 q, c = t % 64 (coalesced either way).
+constexpr int kBlkPer = kSB * kSB / 256;
+
+template <class Acc>
+__device__ __forceinline__ void blk_coord(int q, int &r, int &c) {
+    if (Acc::kRowsFastest) {
+        r = threadIdx.x % kSB;
+        c = threadIdx.x / kSB + 4 * q;
+    } else {
+        r = threadIdx.x / kSB + 4 * q;
+        c = threadIdx.x % kSB;
     }
-    __syncthreads();
-    if (threadIdx.x < kSB) sm.rinv[threadIdx.x] = T(1) / sm.Ld[threadIdx.x][threadIdx.x];
-    __syncthreads();
+}
+
+// Issue the loads of block (r0, c0) of L into registers.  diag: the diagonal
+// block (upper part zero, identity beyond n); otherwise entries beyond n are 0.
+template <typename T, class Acc>
+__device__ __forceinline__ void load_block_regs(const Acc &L, int64_t n, int64_t r0, int64_t c0, bool diag,
+                                                T (&v)[kBlkPer]) {
+    const bool fast = L.blocked();
+    BlockRef<T> b{nullptr, 0, 0};
+    if (fast) b = L.block(r0, c0);
+#pragma unroll
+    for (int q = 0; q < kBlkPer; ++q) {
+        int r, c;
+        blk_coord<Acc>(q, r, c);
+        const int64_t i = r0 + r, j = c0 + c;
+        T x = T(0);
+        if (i < n && j < n) {
+            if (!diag || j <= i) x = fast ? __ldcg(b.p + r * b.rs + c * b.cs) : L(i, j);
+        } else if (diag && i == j) {
+            x = T(1);
+        }
+        v[q] = x;
+    }
+}
+
+// Store a register block into S[r][c] (transpose=false) or S[c][r].
+template <typename T, class Acc>
+__device__ __forceinline__ void store_block_regs(const T (&v)[kBlkPer], T (*S)[kSB + 1], bool transpose) {
+#pragma unroll
+    for (int q = 0; q < kBlkPer; ++q) {
+        int r, c;
+        blk_coord<Acc>(q, r, c);
+        if (transpose) S[c][r] = v[q];
+        else S[r][c] = v[q];
+    }
 }
 
 // Solve with the diagonal block in place on sm.Xs (64 rows x 16 columns):
@@ -118,27 +168,6 @@ __device__ void diag_solve(SolveSmem<T> &sm) {
     __syncthreads();
 }
 
-// Load the 64 x 64 block of L with rows [r0, r0+64) and columns [c0, c0+64)
-// (rows / columns beyond n read as the identity) into Ls[r][c] (transpose=false)
-// or Ls[c][r] (transpose=true).
-template <typename T, class Acc>
-__device__ void load_Lblock(const Acc &L, int64_t n, int64_t r0, int64_t c0, SolveSmem<T> &sm, bool transpose) {
-    for (int e = threadIdx.x; e < kSB * kSB; e += blockDim.x) {
-        int r, c;
-        if (Acc::kRowsFastest) { r = e % kSB; c = e / kSB; }
-        else { r = e / kSB; c = e % kSB; }
-        const int64_t i = r0 + r, j = c0 + c;
-        T v = T(0);
-        if (i < n && j < n) {
-            if (j <= i) v = L(i, j);
-        } else if (i == j) {
-            v = T(1);
-        }
-        if (transpose) sm.Ls[c][r] = v;
-        else sm.Ls[r][c] = v;
-    }
-}
-
 __device__ __forceinline__ bool wait_flag(const int32_t *flag, uint64_t deadline, SolveCtl *ctl, int where) {
     while (!ld_acquire_s32(flag)) {
         if (ld_relaxed_s32(&ctl->status)) return false;
@@ -151,103 +180,96 @@ __device__ __forceinline__ bool wait_flag(const int32_t *flag, uint64_t deadline
     return true;
 }
 
-// Forward sweep: Y = L^{-1} B in place (B column-major, ldb).
-template <typename T, class Acc>
-__global__ void __launch_bounds__(256) solve_fwd_kernel(Acc L, T *B, int64_t ldb, int64_t n, int64_t nrhs,
-                                                        int32_t *flags, SolveCtl *ctl, uint64_t timeout_ns) {
+// One sweep.  FWD: Y = L^{-1} B in place, blocks in increasing order, the
+// block row I gets -L(I, J) y_J for J < I.  Backward: X = L^{-T} Y in place,
+// blocks from the last, block I gets -L(J, I)^T x_J for J > I.  The u-th update
+// of a CTA uses block J(u) = u (forward) or nblk - 1 - u (backward), which the
+// sweep finishes in that same order.
+template <typename T, class Acc, bool FWD>
+__global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t ldb, int64_t n, int64_t nrhs,
+                                                          int32_t *flags, SolveCtl *ctl, uint64_t timeout_ns) {
     __shared__ SolveSmem<T> sm;
     const int nblk = (int)((n + kSB - 1) / kSB);
     const int y = blockIdx.y;
-    if (threadIdx.x == 0) sm.I = (int)atomicAdd(&ctl->tickets[2 * y], 1u);
+    if (threadIdx.x == 0) {
+        sm.I = (int)atomicAdd(&ctl->tickets[2 * y + (FWD ? 0 : 1)], 1u);
+        sm.known = 0;
+    }
     __syncthreads();
-    const int I = sm.I;
-    if (I >= nblk) return;
+    const int t = sm.I;
+    if (t >= nblk) return;
+    const int I = FWD ? t : nblk - 1 - t;
+    const int nupd = t;
+    auto Jof = [&](int u) { return FWD ? u : nblk - 1 - u; };
     const int64_t c0 = (int64_t)y * kRC;
     const int c = threadIdx.x % kRC, rq = threadIdx.x / kRC;  // rows rq + 16 q
     int32_t *fl = flags + (size_t)y * nblk;
     const uint64_t deadline = global_ns() + timeout_ns;
-    load_diag<T>(L, n, (int64_t)I * kSB, sm);
+    const int64_t rI = (int64_t)I * kSB;
+    T lr[kBlkPer];
+    // the first off-diagonal block, then the diagonal block (through Ld)
+    if (nupd > 0) {
+        const int64_t rJ = (int64_t)Jof(0) * kSB;
+        load_block_regs<T>(L, n, FWD ? rI : rJ, FWD ? rJ : rI, false, lr);
+    }
+    {
+        T dr[kBlkPer];
+        load_block_regs<T>(L, n, rI, rI, true, dr);
+        store_block_regs<T, Acc>(dr, sm.Ld, false);
+    }
     T acc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int64_t i = (int64_t)I * kSB + rq + 16 * q;
+        const int64_t i = rI + rq + 16 * q;
         acc[q] = (i < n && c0 + c < nrhs) ? B[(c0 + c) * ldb + i] : T(0);
     }
-    for (int J = 0; J < I; ++J) {
+    __syncthreads();
+    if (threadIdx.x < kSB) sm.rinv[threadIdx.x] = T(1) / sm.Ld[threadIdx.x][threadIdx.x];
+    // solution values of the next finished block, prefetched into registers
+    constexpr int kXPer = kSB * kRC / 256;
+    T xr[kXPer];
+    bool xpre = false;
+    for (int u = 0; u < nupd; ++u) {
+        const int J = Jof(u);
         if (threadIdx.x == 0) {
-            if (!wait_flag(fl + J, deadline, ctl, 10)) sm.I = -1;
-            else fence_acq_rel();
+            int known = sm.known;
+            if (u >= known) {
+                if (!wait_flag(fl + J, deadline, ctl, FWD ? 10 : 20)) {
+                    sm.I = -1;
+                } else {
+                    known = u + 1;
+                    // note the further blocks that are already finished
+                    while (known < nupd && known < u + 32 && ld_acquire_s32(fl + Jof(known))) ++known;
+                    fence_acq_rel();
+                }
+                sm.known = known;
+            }
         }
         __syncthreads();
         if (sm.I < 0) return;
-        load_Lblock<T>(L, n, (int64_t)I * kSB, (int64_t)J * kSB, sm, false);
-        for (int e = threadIdx.x; e < kSB * kRC; e += blockDim.x) {
-            const int k = e / kRC, cc = e % kRC;
-            const int64_t i = (int64_t)J * kSB + k;
-            sm.Xs[k][cc] = (i < n && c0 + cc < nrhs) ? __ldcg(B + (c0 + cc) * ldb + i) : T(0);
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < kSB; ++k) {
-            const T yk = sm.Xs[k][c];
+        store_block_regs<T, Acc>(lr, sm.Ls, !FWD);
+        const int64_t rJ = (int64_t)J * kSB;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fma(-sm.Ls[rq + 16 * q][k], yk, acc[q]);
+        for (int q = 0; q < kXPer; ++q) {
+            const int e = threadIdx.x + 256 * q, k = e / kRC, cc = e % kRC;
+            if (!xpre) {
+                const int64_t i = rJ + k;
+                xr[q] = (i < n && c0 + cc < nrhs) ? __ldcg(B + (c0 + cc) * ldb + i) : T(0);
+            }
+            sm.Xs[k][cc] = xr[q];
         }
-        __syncthreads();
-    }
-    // diagonal block: L_II y = acc
+        if (u + 1 < nupd) {
+            const int64_t rN = (int64_t)Jof(u + 1) * kSB;
+            load_block_regs<T>(L, n, FWD ? rI : rN, FWD ? rN : rI, false, lr);
+            xpre = u + 1 < sm.known;
+            if (xpre) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sm.Xs[rq + 16 * q][c] = acc[q];
-    __syncthreads();
-    diag_solve<T, true>(sm);
-    for (int e = threadIdx.x; e < kSB * kRC; e += blockDim.x) {
-        const int k = e / kRC, cc = e % kRC;
-        const int64_t i = (int64_t)I * kSB + k;
-        if (i < n && c0 + cc < nrhs) B[(c0 + cc) * ldb + i] = sm.Xs[k][cc];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        fence_acq_rel();
-        st_release_s32(fl + I, 1);
-    }
-}
-
-// Backward sweep: X = L^{-T} Y in place; tickets run the blocks from the last.
-template <typename T, class Acc>
-__global__ void __launch_bounds__(256) solve_bwd_kernel(Acc L, T *B, int64_t ldb, int64_t n, int64_t nrhs,
-                                                        int32_t *flags, SolveCtl *ctl, uint64_t timeout_ns) {
-    __shared__ SolveSmem<T> sm;
-    const int nblk = (int)((n + kSB - 1) / kSB);
-    const int y = blockIdx.y;
-    if (threadIdx.x == 0) sm.I = (int)atomicAdd(&ctl->tickets[2 * y + 1], 1u);
-    __syncthreads();
-    const int t = sm.I;
-    if (t >= nblk) return;
-    const int I = nblk - 1 - t;
-    const int64_t c0 = (int64_t)y * kRC;
-    const int c = threadIdx.x % kRC, rq = threadIdx.x / kRC;
-    int32_t *fl = flags + (size_t)y * nblk;
-    const uint64_t deadline = global_ns() + timeout_ns;
-    load_diag<T>(L, n, (int64_t)I * kSB, sm);
-    T acc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t i = (int64_t)I * kSB + rq + 16 * q;
-        acc[q] = (i < n && c0 + c < nrhs) ? B[(c0 + c) * ldb + i] : T(0);
-    }
-    for (int J = nblk - 1; J > I; --J) {
-        if (threadIdx.x == 0) {
-            if (!wait_flag(fl + J, deadline, ctl, 20)) sm.I = -1;
-            else fence_acq_rel();
-        }
-        __syncthreads();
-        if (sm.I < 0) return;
-        // Ls[r][k] = L(J*64 + k, I*64 + r): the transpose of block (J, I)
-        load_Lblock<T>(L, n, (int64_t)J * kSB, (int64_t)I * kSB, sm, true);
-        for (int e = threadIdx.x; e < kSB * kRC; e += blockDim.x) {
-            const int k = e / kRC, cc = e % kRC;
-            const int64_t i = (int64_t)J * kSB + k;
-            sm.Xs[k][cc] = (i < n && c0 + cc < nrhs) ? __ldcg(B + (c0 + cc) * ldb + i) : T(0);
+                for (int q = 0; q < kXPer; ++q) {
+                    const int e = threadIdx.x + 256 * q, k = e / kRC, cc = e % kRC;
+                    const int64_t i = rN + k;
+                    xr[q] = (i < n && c0 + cc < nrhs) ? __ldcg(B + (c0 + cc) * ldb + i) : T(0);
+                }
+            }
         }
         __syncthreads();
 #pragma unroll 8
@@ -256,16 +278,16 @@ __global__ void __launch_bounds__(256) solve_bwd_kernel(Acc L, T *B, int64_t ldb
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[q] = fma(-sm.Ls[rq + 16 * q][k], xk, acc[q]);
         }
-        __syncthreads();
     }
-    // diagonal block: L_II^T x = acc  (Ld[r][c] = L_II(r, c), lower)
+    __syncthreads();
+    // diagonal block: L_II y = acc (forward) or L_II^T x = acc (backward)
 #pragma unroll
     for (int q = 0; q < 4; ++q) sm.Xs[rq + 16 * q][c] = acc[q];
     __syncthreads();
-    diag_solve<T, false>(sm);
+    diag_solve<T, FWD>(sm);
     for (int e = threadIdx.x; e < kSB * kRC; e += blockDim.x) {
         const int k = e / kRC, cc = e % kRC;
-        const int64_t i = (int64_t)I * kSB + k;
+        const int64_t i = rI + k;
         if (i < n && c0 + cc < nrhs) B[(c0 + cc) * ldb + i] = sm.Xs[k][cc];
     }
     __syncthreads();
@@ -296,8 +318,8 @@ int launch_solve(const Acc &L, T *B, int64_t ldb, int64_t n, int64_t nrhs, void 
     CHOL_CUDA(cudaMemsetAsync(ws, 0, solve_ws_bytes(n, nrhs), st));
     const uint64_t tns = (uint64_t)(timeout_s * 1e9);
     const dim3 grid((unsigned)nblk, (unsigned)ny);
-    solve_fwd_kernel<T, Acc><<<grid, 256, 0, st>>>(L, B, ldb, n, nrhs, flags, ctl, tns);
-    solve_bwd_kernel<T, Acc><<<grid, 256, 0, st>>>(L, B, ldb, n, nrhs, flags + nblk * ny, ctl, tns);
+    solve_sweep_kernel<T, Acc, true><<<grid, 256, 0, st>>>(L, B, ldb, n, nrhs, flags, ctl, tns);
+    solve_sweep_kernel<T, Acc, false><<<grid, 256, 0, st>>>(L, B, ldb, n, nrhs, flags + nblk * ny, ctl, tns);
     CHOL_CUDA(cudaGetLastError());
     return CHOL_OK;
 }
