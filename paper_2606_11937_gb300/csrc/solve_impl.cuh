@@ -8,10 +8,13 @@
 // finished blocks in order as their ready flags appear (acquire): the next
 // factor block is loaded into registers while the current one is applied, and
 // one flag poll also takes note of the further blocks that are already
-// finished, whose solution values are then prefetched the same way.  It then
-// solves its diagonal block (loaded before the waits; one warp per pair of
-// right-hand sides, shuffles instead of block barriers), stores the result
-// and releases its own flag.
+// finished, whose solution values are then prefetched the same way.  Before
+// its waits it inverts its diagonal block (W = L_II^{-1}, one column per
+// thread), so that on the sweep's critical path the diagonal step is the
+// product W y (or W^T x) rather than 64 dependent substitution steps; a block
+// whose kappa_inf = ||L_II|| ||W|| exceeds kSolveKappa keeps the substitution
+// (one warp per pair of right-hand sides, shuffles instead of block
+// barriers).  It stores the result and releases its own flag.
 // Every wait is bounded by a %globaltimer deadline after which the kernel
 // records CHOL_ERR_TIMEOUT and returns.  grid.y splits the right-hand sides
 // into slices of kRC columns, each with its own tickets and flags.
@@ -67,14 +70,18 @@ struct SolveCtl {
     unsigned int tickets[2 * 4096];  // per rhs slice: forward, backward (grid.y <= 4096)
 };
 
+constexpr double kSolveKappa = 65536.0;  // largest kappa_inf of a diagonal block applied by its inverse
+
 template <typename T>
 struct SolveSmem {
-    T Ls[kSB][kSB + 1];   // off-diagonal block being applied
-    T Ld[kSB][kSB + 1];   // this CTA's diagonal block, loaded before the wait loop
-    T rinv[kSB];          // reciprocals of its diagonal
+    T Ls[kSB][kSB + 1];   // off-diagonal block being applied (first the diagonal block)
+    T W[kSB][kSB + 1];    // inverse of the diagonal block, or the block itself (substitution)
+    T rinv[kSB];          // reciprocals of the diagonal block's diagonal
     T Xs[kSB][kRC + 1];
+    T nrm[2][2];          // per warp of the first two: max row sums of |L_II| and |W|
     int I;
     int known;            // leading blocks of the sweep known to be finished
+    int subst;            // diagonal block too ill-conditioned for its inverse
 };
 
 // Register share of one 64 x 64 block: thread t holds 16 elements, (r, c)
@@ -133,7 +140,7 @@ __device__ __forceinline__ void store_block_regs(const T (&v)[kBlkPer], T (*S)[k
 // and 2w+1; lane l owns rows l and l+32 and receives each solved entry by a
 // shuffle, so the 64 steps need no block barrier.  Ends with a barrier.
 template <typename T, bool FWD>
-__device__ void diag_solve(SolveSmem<T> &sm) {
+__device__ void diag_solve(SolveSmem<T> &sm, const T (*Ld)[kSB + 1]) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int c0 = 2 * warp, c1 = 2 * warp + 1;
     T a0 = sm.Xs[lane][c0], a1 = sm.Xs[lane][c1], b0 = sm.Xs[lane + 32][c0], b1 = sm.Xs[lane + 32][c1];
@@ -151,12 +158,12 @@ __device__ void diag_solve(SolveSmem<T> &sm) {
         // FWD: rows i > k get -L(i, k) x_k; backward: rows i < k get -L(k, i) x_k
         const int i0 = lane, i1 = lane + 32;
         if (FWD ? i0 > k : i0 < k) {
-            const T l = FWD ? sm.Ld[i0][k] : sm.Ld[k][i0];
+            const T l = FWD ? Ld[i0][k] : Ld[k][i0];
             a0 = fma(-l, x0, a0);
             a1 = fma(-l, x1, a1);
         }
         if (FWD ? i1 > k : i1 < k) {
-            const T l = FWD ? sm.Ld[i1][k] : sm.Ld[k][i1];
+            const T l = FWD ? Ld[i1][k] : Ld[k][i1];
             b0 = fma(-l, x0, b0);
             b1 = fma(-l, x1, b1);
         }
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
     {
         T dr[kBlkPer];
         load_block_regs<T>(L, n, rI, rI, true, dr);
-        store_block_regs<T, Acc>(dr, sm.Ld, false);
+        store_block_regs<T, Acc>(dr, sm.Ls, false);
     }
     T acc[4];
 #pragma unroll
@@ -224,7 +231,45 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
         acc[q] = (i < n && c0 + c < nrhs) ? B[(c0 + c) * ldb + i] : T(0);
     }
     __syncthreads();
-    if (threadIdx.x < kSB) sm.rinv[threadIdx.x] = T(1) / sm.Ld[threadIdx.x][threadIdx.x];
+    if (threadIdx.x < kSB) sm.rinv[threadIdx.x] = T(1) / sm.Ls[threadIdx.x][threadIdx.x];
+    __syncthreads();
+    // W = L_II^{-1} by forward substitution on the identity, column c by thread c
+    if (threadIdx.x < kSB) {
+        const int cw = threadIdx.x;
+        for (int i = 0; i < cw; ++i) sm.W[i][cw] = T(0);
+        sm.W[cw][cw] = sm.rinv[cw];
+        for (int i = cw + 1; i < kSB; ++i) {
+            T t = T(0);
+            for (int k = cw; k < i; ++k) t = fma(sm.Ls[i][k], sm.W[k][cw], t);
+            sm.W[i][cw] = -t * sm.rinv[i];
+        }
+    }
+    __syncthreads();
+    // kappa_inf = ||L_II||_inf ||W||_inf (row sums, thread r for row r)
+    if (threadIdx.x < kSB) {
+        T sl = T(0), sw = T(0);
+        for (int k = 0; k < kSB; ++k) {
+            sl += fabs(sm.Ls[threadIdx.x][k]);
+            sw += fabs(sm.W[threadIdx.x][k]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            sl = fmax(sl, __shfl_xor_sync(0xffffffffu, sl, o));
+            sw = fmax(sw, __shfl_xor_sync(0xffffffffu, sw, o));
+        }
+        if (threadIdx.x % 32 == 0) {
+            sm.nrm[threadIdx.x / 32][0] = sl;
+            sm.nrm[threadIdx.x / 32][1] = sw;
+        }
+    }
+    __syncthreads();
+    {
+        const double kap = (double)fmax(sm.nrm[0][0], sm.nrm[1][0]) * (double)fmax(sm.nrm[0][1], sm.nrm[1][1]);
+        const bool subst = !(kap <= kSolveKappa);  // also on NaN / Inf
+        if (subst) {  // keep the block itself for the substitution
+            for (int e = threadIdx.x; e < kSB * kSB; e += blockDim.x) sm.W[e / kSB][e % kSB] = sm.Ls[e / kSB][e % kSB];
+        }
+        if (threadIdx.x == 0) sm.subst = subst;
+    }
     // solution values of the next finished block, prefetched into registers
     constexpr int kXPer = kSB * kRC / 256;
     T xr[kXPer];
@@ -240,7 +285,6 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
                     known = u + 1;
                     // note the further blocks that are already finished
                     while (known < nupd && known < u + 32 && ld_acquire_s32(fl + Jof(known))) ++known;
-                    fence_acq_rel();
                 }
                 sm.known = known;
             }
@@ -284,17 +328,33 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
 #pragma unroll
     for (int q = 0; q < 4; ++q) sm.Xs[rq + 16 * q][c] = acc[q];
     __syncthreads();
-    diag_solve<T, FWD>(sm);
+    if (!sm.subst) {
+        // y = W acc (forward), x = W^T acc (backward); W is zero above its diagonal
+        T y[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 8
+        for (int k = 0; k < kSB; ++k) {
+            const T xk = sm.Xs[k][c];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = rq + 16 * q;
+                y[q] = fma(FWD ? sm.W[r][k] : sm.W[k][r], xk, y[q]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sm.Xs[rq + 16 * q][c] = y[q];
+        __syncthreads();
+    } else {
+        diag_solve<T, FWD>(sm, sm.W);
+    }
     for (int e = threadIdx.x; e < kSB * kRC; e += blockDim.x) {
         const int k = e / kRC, cc = e % kRC;
         const int64_t i = rI + k;
         if (i < n && c0 + cc < nrhs) B[(c0 + cc) * ldb + i] = sm.Xs[k][cc];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        fence_acq_rel();
-        st_release_s32(fl + I, 1);
-    }
+    // the barrier orders every thread's stores before this release (cumulative)
+    if (threadIdx.x == 0) st_release_s32(fl + I, 1);
 }
 
 // Workspace bytes for a solve of order n with nrhs right-hand sides.
