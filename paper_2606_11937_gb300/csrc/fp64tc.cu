@@ -51,7 +51,9 @@ __device__ __forceinline__ int oz_potrf128(double *A, OzSmem &sm) {
 // W are finished one after the other (entry (k, c) = (R(k, c) - sum over
 // m = k0..k-1 of L(k, m) W(m, c)) / L(k, k), R the updated right-hand side),
 // then the rows below receive them as one rank-4 update R(i, c) -=
-// sum_q L(i, k0+q) W(k0+q, c).  W(i, c), c < i, is stored transposed in the
+// sum_q L(i, k0+q) W(k0+q, c) (the next block's rows by warps 0..3, which
+// then finish that block, the others by the remaining warps).  The
+// reciprocals of L's diagonal come from the POTRF (its shared memory).  W(i, c), c < i, is stored transposed in the
 // strict upper part of S (S(c, i)), its diagonal in a separate vector.  Writes
 // W (row-major, zero above the diagonal) to Wout and returns
 // kappa_inf = ||L||_inf ||W||_inf.  All threads; ends with a barrier.
@@ -77,41 +79,59 @@ __device__ double oz_trtri128(OzSmem &sm, double *Wout) {
     __syncthreads();
     double nL = 0.0;
     for (int w = 0; w < nw; ++w) nL = fmax(nL, red[w]);
-    for (int k0 = 0; k0 < kOzNb; k0 += 4) {
-        // rows k0 .. k0+3 of W by warp 0: lane l owns columns l, l+32, ..., so
-        // the rows of a block depend on each other only within a lane (and on
-        // the diagonal entries, ordered by the warp barriers)
-        if (warp == 0) {
-            for (int q = 0; q < 4; ++q) {
-                const int k = k0 + q;
-                const double rk = 1.0 / S[k * P + k];
-                for (int c = lane; c <= k; c += 32) {
-                    if (c == k) {
-                        wd[k] = rk;
-                    } else {
-                        double v = S[c * P + k];
-                        for (int mm = k0; mm < k; ++mm) {
-                            const double wmc = c < mm ? S[c * P + mm] : (c == mm ? wd[mm] : 0.0);
-                            v = fma(-S[k * P + mm], wmc, v);
-                        }
-                        S[c * P + k] = v * rk;
-                    }
+    // the reciprocals of L's diagonal, left by the shared-memory POTRF
+    const double *rcp = reinterpret_cast<const double *>(reinterpret_cast<const uint8_t *>(sm.B) + kPotrf128RcpOff);
+    // rows k0 .. k0+3 of W by the 128 panel threads: thread c owns column c, so
+    // the rows of a block depend on each other only within a thread (the
+    // diagonal entry W(c, c) included)
+    auto w_block = [&](int k0) {
+        const int c = t;
+        for (int q = 0; q < 4; ++q) {
+            const int k = k0 + q;
+            const double rk = rcp[k];
+            if (c == k) {
+                wd[k] = rk;
+            } else if (c < k) {
+                double v = S[c * P + k];
+                for (int mm = k0; mm < k; ++mm) {
+                    const double wmc = c < mm ? S[c * P + mm] : (c == mm ? wd[mm] : 0.0);
+                    v = fma(-S[k * P + mm], wmc, v);
                 }
-                __syncwarp();
+                S[c * P + k] = v * rk;
             }
         }
-        __syncthreads();
-        // rows i >= k0 + 4, columns c <= k0 + 3: R(i, c) -= sum_q L(i, k0+q) W(k0+q, c)
+    };
+    // W(r, c) of a finished block row r (zero above the diagonal)
+    auto wrc = [&](int r, int c) { return c < r ? S[c * P + r] : (c == r ? wd[r] : 0.0); };
+    if (t < kPotrfPanelThreads) w_block(0);
+    __syncthreads();
+    // With lookahead: while warps 4.. apply block k0 to the rows below the next
+    // block, warps 0..3 apply it to the next block's four rows and compute them.
+    // R(i, c) -= sum_q L(i, k0+q) W(k0+q, c) for rows i >= k0 + 4, columns
+    // c <= k0 + 3; every element receives the blocks in ascending order.
+    for (int k0 = 0; k0 < kOzNb; k0 += 4) {
         const int i0 = k0 + 4;
-        if (i0 < kOzNb) {
-            for (int c = warp; c < i0; c += nw) {
+        if (i0 >= kOzNb) break;
+        const int i1 = i0 + 4 < kOzNb ? i0 + 4 : kOzNb;
+        if (t < kPotrfPanelThreads) {
+            for (int e = t; e < 4 * i0; e += kPotrfPanelThreads) {
+                const int i = i0 + (e & 3), c = e >> 2;
+                if (i < i1) {
+                    double v = S[c * P + i];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) v = fma(-S[i * P + k0 + q], wrc(k0 + q, c), v);
+                    S[c * P + i] = v;
+                }
+            }
+            potrf_panel_sync();
+            w_block(i0);
+        } else {
+            constexpr int pw = kPotrfPanelThreads / 32;
+            for (int c = warp - pw; c < i0; c += nw - pw) {
                 double wq[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int r = k0 + q;
-                    wq[q] = c < r ? S[c * P + r] : (c == r ? wd[r] : 0.0);
-                }
-                for (int i = i0 + lane; i < kOzNb; i += 32) {
+                for (int q = 0; q < 4; ++q) wq[q] = wrc(k0 + q, c);
+                for (int i = i1 + lane; i < kOzNb; i += 32) {
                     double v = S[c * P + i];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) v = fma(-S[i * P + k0 + q], wq[q], v);

@@ -8,28 +8,40 @@
 namespace chol {
 
 constexpr int kPotrfNb = 128;
-// padded 128 x 129 binary64 tile + (i, k) table of the lower triangle
-constexpr size_t kPotrf128SmemBytes = (size_t)kPotrfNb * (kPotrfNb + 1) * 8 + (size_t)kPotrfNb * (kPotrfNb + 1);
+// padded 128 x 129 binary64 tile + (i, k) table of the lower triangle + the
+// reciprocals of the factor's diagonal
+constexpr size_t kPotrf128TabOff = (size_t)kPotrfNb * (kPotrfNb + 1) * 8;
+constexpr size_t kPotrf128RcpOff = kPotrf128TabOff + (size_t)kPotrfNb * (kPotrfNb + 1);
+constexpr size_t kPotrf128SmemBytes = kPotrf128RcpOff + (size_t)kPotrfNb * 8;
+constexpr int kPotrfPanelThreads = 128;  // warps 0..3, one per SM sub-partition
+
+// the panel threads' named barrier (id 4; no other code of a task uses it)
+__device__ __forceinline__ void potrf_panel_sync() { asm volatile("bar.sync 4, 128;" ::: "memory"); }
 
 // Cholesky, in binary64, of a 128 x 128 diagonal tile (row-major, lower part
 // read and written; T = double, or float widened on load and rounded on
 // store) in shared memory, right-looking: columns are factored four at a
-// time (the panel by one warp, with warp barriers only) and each block of four
-// is applied to the trailing lower triangle as one rank-4 update by all
-// threads.  Every element sees the same operations in the same
-// order as the Crout formulas (fused multiply-subtracts in ascending column
-// order), the division by the pivot being a multiplication by its reciprocal.  The trailing elements are visited through a
-// table of (i, k) in column-major lower order, so the active ones form a
-// contiguous suffix and all threads stay busy.  All threads; smem holds
-// kPotrf128SmemBytes (the padded tile stays there for the caller); returns 0
-// or the 1-based local column whose pivot is not positive (or NaN).  Ends with
-// a barrier.
+// time and each block of four is applied to the trailing lower triangle as
+// one rank-4 update.  With lookahead: while warps 4.. apply panel p to the
+// columns right of panel p + 1, warps 0..3 (one per SM sub-partition, so the
+// panel has the binary64 pipes of all four) apply it to panel p + 1's four
+// columns and factor them (a named barrier between columns), so the panels'
+// sequential work overlaps the trailing updates.  Every element sees the same operations
+// in the same order as the Crout formulas (fused multiply-subtracts in
+// ascending column order), the division by the pivot being a multiplication
+// by its reciprocal.  The trailing elements are visited through a table of
+// (i, k) in column-major lower order, so the active ones form a contiguous
+// suffix and all threads stay busy.  All threads (at least 256); smem holds
+// kPotrf128SmemBytes (the padded tile and the reciprocals of its diagonal,
+// at kPotrf128RcpOff, stay there for the caller); returns 0 or the 1-based
+// local column whose pivot is not positive (or NaN).  Ends with a barrier.
 template <typename T>
 __device__ int smem_potrf128(T *A, uint8_t *smem) {
     constexpr int N = kPotrfNb;
     constexpr int P = N + 1;  // padded row
     double *S = reinterpret_cast<double *>(smem);
-    uint16_t *tab = reinterpret_cast<uint16_t *>(smem + N * P * 8);
+    uint16_t *tab = reinterpret_cast<uint16_t *>(smem + kPotrf128TabOff);
+    double *rcp = reinterpret_cast<double *>(smem + kPotrf128RcpOff);
     const int t = threadIdx.x, nt = blockDim.x;
     constexpr int kTri = N * (N + 1) / 2;
     for (int e = t; e < N * N; e += nt) {
@@ -41,48 +53,70 @@ __device__ int smem_potrf128(T *A, uint8_t *smem) {
         for (int i = k; i < N; ++i) tab[off + i - k] = (uint16_t)((i << 8) | k);
     }
     __syncthreads();
-    __shared__ int s_fail;
-    const int warp = t / 32, lane = t % 32;
-    for (int j0 = 0; j0 < N; j0 += 4) {
-        // the panel (columns j0 .. j0+3, rows j0 .. N-1) by warp 0 alone: lane l
-        // owns rows l, l+32, ...; only warp barriers between the columns
-        if (warp == 0) {
-            int fail = 0;
-            for (int q = 0; q < 4 && !fail; ++q) {
-                const int j = j0 + q;
-                const double djj = S[j * P + j];
-                __syncwarp();
-                if (!(djj > 0.0)) {  // uniform: every lane read the same value
-                    fail = j + 1;
-                    break;
-                }
-                const double d = sqrt(djj), rd = 1.0 / d;
-                if (lane == 0) S[j * P + j] = d;
-                for (int i = j + 1 + lane; i < N; i += 32) S[i * P + j] *= rd;
-                __syncwarp();
-                for (int c = j + 1; c < j0 + 4; ++c) {
-                    const double scj = S[c * P + j];
-                    for (int i = c + lane; i < N; i += 32) S[i * P + c] = fma(-S[i * P + j], scj, S[i * P + c]);
-                }
-                __syncwarp();
+    // failure of the panel factored in step it (it = j0 / 4) at s_fail[it & 1]:
+    // read at the top of step it + 1 while the panel threads write the other slot
+    __shared__ int s_fail[2];
+    // table offset of column k's first element (k <= N)
+    auto col_off = [](int k) { return k * N - k * (k - 1) / 2; };
+    constexpr int PT = kPotrfPanelThreads;
+    // the panel (columns j0 .. j0+3, rows j0 .. N-1) by the panel threads
+    // (thread t < 128 owns row j + 1 + t of column j): every one computes the
+    // pivot's root and reciprocal, a named barrier separates the columns
+    auto factor_panel = [&](int j0) -> int {
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + q;
+            const double djj = S[j * P + j];
+            potrf_panel_sync();
+            if (!(djj > 0.0)) return j + 1;  // uniform: every thread read the same value
+            const double d = sqrt(djj), rd = 1.0 / d;
+            if (t == 0) {
+                S[j * P + j] = d;
+                rcp[j] = rd;
             }
-            if (lane == 0) s_fail = fail;
+            for (int i = j + 1 + t; i < N; i += PT) S[i * P + j] *= rd;
+            potrf_panel_sync();
+            for (int c = j + 1; c < j0 + 4; ++c) {
+                const double scj = S[c * P + j];
+                for (int i = c + t; i < N; i += PT) S[i * P + c] = fma(-S[i * P + j], scj, S[i * P + c]);
+            }
+            potrf_panel_sync();
         }
-        __syncthreads();
-        if (s_fail) {
-            const int f = s_fail;
-            __syncthreads();
-            return f;
-        }
-        // trailing rank-4 update of the elements (i, k), j0 + 4 <= k <= i
-        const int k0 = j0 + 4;
-        const int off = k0 * N - k0 * (k0 - 1) / 2;
-        for (int e = off + t; e < kTri; e += nt) {
+        return 0;
+    };
+    // rank-4 update of the table entries [e0, e1) with panel j0 by threads
+    // first .. first + count - 1 (the thread's index relative to first is r)
+    auto rank4 = [&](int j0, int e0, int e1, int r, int count) {
+        for (int e = e0 + r; e < e1; e += count) {
             const int ik = tab[e], i = ik >> 8, k = ik & 255;
             double v = S[i * P + k];
 #pragma unroll
             for (int q = 0; q < 4; ++q) v = fma(-S[i * P + j0 + q], S[k * P + j0 + q], v);
             S[i * P + k] = v;
+        }
+    };
+    if (t < PT) {
+        const int f = factor_panel(0);
+        if (t == 0) s_fail[0] = f;
+    }
+    __syncthreads();
+    for (int j0 = 0; j0 < N; j0 += 4) {
+        const int it = j0 / 4;
+        const int fl = s_fail[it & 1];
+        if (fl) {
+            __syncthreads();
+            return fl;
+        }
+        const int k0 = j0 + 4;  // the next panel
+        if (k0 >= N) break;
+        const int k1 = k0 + 4 < N ? k0 + 4 : N;
+        if (t < PT) {
+            // panel j0 applied to the next panel's columns, then that panel factored
+            rank4(j0, col_off(k0), col_off(k1), t, PT);
+            potrf_panel_sync();
+            const int f = factor_panel(k0);
+            if (t == 0) s_fail[(it + 1) & 1] = f;
+        } else {
+            rank4(j0, col_off(k1), kTri, t - PT, nt - PT);
         }
         __syncthreads();
     }
