@@ -100,12 +100,24 @@ __device__ __forceinline__ uint16_t small_int_bf16(uint32_t a, uint32_t neg) {
 // to o[s * sstride + c]; `negate` splits -v.
 __device__ __forceinline__ int ozaki_split_row(const double (&v)[4], uint16_t *o, size_t sstride, bool negate) {
     const int lane = threadIdx.x % 32;
-    double m = 0.0;
+    // e = the frexp exponent of the row's largest magnitude m (m = f 2^e,
+    // f in [0.5, 1), so |row| < 2^e), NaNs ignored, 0 if m is 0 or infinite;
+    // found on the integer pipes: the magnitude bits of non-negative doubles
+    // order like the values (GB300's binary64 pipe is the scarce one)
+    unsigned long long mb = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) m = fmax(m, fabs(v[q]));
-    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    for (int q = 0; q < 4; ++q) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v[q]) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long mag = b > 0x7FF0000000000000ull ? 0ull : b;  // NaN
+        mb = mag > mb ? mag : mb;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mb, off);
+        mb = o > mb ? o : mb;
+    }
     int e = 0;
-    if (m > 0.0 && isfinite(m)) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): |row| < 2^e
+    const int emax = (int)(mb >> 52);
+    if (mb != 0 && emax != 2047) e = emax ? emax - 1022 : (63 - __clzll((long long)mb)) - 1073;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const unsigned long long bits = (unsigned long long)__double_as_longlong(v[q]);
@@ -140,15 +152,27 @@ __device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32
                                    bool transpose = false) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
     uint16_t *out = reinterpret_cast<uint16_t *>(slices);
-    for (int r = warp; r < kOzNb; r += nwarps) {
-        double v[4];
+    // four rows per warp at a time: their loads are in flight together
+    constexpr int kRows = 4;
+    for (int r0 = warp; r0 < kOzNb; r0 += kRows * nwarps) {
+        double v[kRows][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int c = lane + 32 * q;
-            v[q] = __ldcg(T + (transpose ? (size_t)c * kOzNb + r : (size_t)r * kOzNb + c));
+        for (int j = 0; j < kRows; ++j) {
+            const int r = r0 + j * nwarps;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = lane + 32 * q;
+                v[j][q] = r < kOzNb ? __ldcg(T + (transpose ? (size_t)c * kOzNb + r : (size_t)r * kOzNb + c)) : 0.0;
+            }
         }
-        const int e = ozaki_split_row(v, out + (size_t)r * kOzNb, (size_t)kOzNb * kOzNb, negate);
-        if (lane == 0) rexp[r] = e;
+#pragma unroll
+        for (int j = 0; j < kRows; ++j) {
+            const int r = r0 + j * nwarps;
+            if (r < kOzNb) {
+                const int e = ozaki_split_row(v[j], out + (size_t)r * kOzNb, (size_t)kOzNb * kOzNb, negate);
+                if (lane == 0) rexp[r] = e;
+            }
+        }
     }
     fence_proxy_async_global();
     __syncthreads();
