@@ -91,13 +91,18 @@ __device__ __forceinline__ uint16_t small_int_bf16(uint32_t a, uint32_t neg) {
     return (uint16_t)((neg << 15) | ((127u + msb) << 7) | mant);
 }
 
-// Split one row of 128 binary64 values (v[q] is column lane + 32 q; one
+// Column of a row that lane `lane` holds in v[q] for ozaki_split_row: each
+// lane owns the column pairs (2 lane, 2 lane + 1) and (64 + 2 lane, 65 + 2 lane),
+// so every slice is written as packed bf16 pairs.
+__device__ __forceinline__ int oz_col(int lane, int q) { return 2 * lane + (q & 1) + 64 * (q >> 1); }
+
+// Split one row of 128 binary64 values (v[q] is column oz_col(lane, q); one
 // warp) into 8 bf16 slices and return the row exponent e (|row| < 2^e).
 // With x = v 2^-e in (-1, 1) and X = floor(|x| 2^56), slice s (1-based) is
 // sign(x) times bits [56 - 7s, 63 - 7s) of X -- the digits the recursion
 // t = 128 x, a = trunc(t), x = t - a produces -- computed with integer
 // operations on the binary64 encoding.  Slice s (0-based) of column c goes
-// to o[s * sstride + c]; `negate` splits -v.
+// to o[s * sstride + c] (o and sstride even); `negate` splits -v.
 __device__ __forceinline__ int ozaki_split_row(const double (&v)[4], uint16_t *o, size_t sstride, bool negate) {
     const int lane = threadIdx.x % 32;
     // e = the frexp exponent of the row's largest magnitude m (m = f 2^e,
@@ -118,10 +123,12 @@ __device__ __forceinline__ int ozaki_split_row(const double (&v)[4], uint16_t *o
     int e = 0;
     const int emax = (int)(mb >> 52);
     if (mb != 0 && emax != 2047) e = emax ? emax - 1022 : (63 - __clzll((long long)mb)) - 1073;
+    unsigned long long Xq[4];
+    uint32_t ng[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const unsigned long long bits = (unsigned long long)__double_as_longlong(v[q]);
-        const uint32_t neg = (uint32_t)(bits >> 63) ^ (negate ? 1u : 0u);
+        ng[q] = (uint32_t)(bits >> 63) ^ (negate ? 1u : 0u);
         const int expo = (int)((bits >> 52) & 0x7FF);
         unsigned long long M = bits & ((1ull << 52) - 1);
         int qexp;                      // |v| = M 2^qexp
@@ -131,14 +138,17 @@ __device__ __forceinline__ int ozaki_split_row(const double (&v)[4], uint16_t *o
             qexp = expo - 1075;
         }
         const int sh = qexp - e + 56;  // X = floor(M 2^sh) < 2^56
-        unsigned long long X;
-        if (sh >= 0) X = M << sh;
-        else X = sh <= -64 ? 0ull : (M >> (-sh));
-        uint16_t *oc = o + lane + 32 * q;
+        if (sh >= 0) Xq[q] = M << sh;
+        else Xq[q] = sh <= -64 ? 0ull : (M >> (-sh));
+    }
+    // slice s of the two columns of a pair, stored as one packed bf16 word
 #pragma unroll
-        for (int s = 0; s < kOzS; ++s) {
-            const uint32_t a = (uint32_t)((X >> (49 - 7 * s)) & 127u);
-            oc[(size_t)s * sstride] = small_int_bf16(a, neg);
+    for (int s = 0; s < kOzS; ++s) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t lo = small_int_bf16((uint32_t)((Xq[2 * h] >> (49 - 7 * s)) & 127u), ng[2 * h]);
+            const uint32_t hi = small_int_bf16((uint32_t)((Xq[2 * h + 1] >> (49 - 7 * s)) & 127u), ng[2 * h + 1]);
+            *reinterpret_cast<uint32_t *>(o + (size_t)s * sstride + 2 * lane + 64 * h) = lo | (hi << 16);
         }
     }
     return e;
@@ -159,10 +169,19 @@ __device__ inline void ozaki_split(const double *T, __nv_bfloat16 *slices, int32
 #pragma unroll
         for (int j = 0; j < kRows; ++j) {
             const int r = r0 + j * nwarps;
+            if (r >= kOzNb) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int c = lane + 32 * q;
-                v[j][q] = r < kOzNb ? __ldcg(T + (transpose ? (size_t)c * kOzNb + r : (size_t)r * kOzNb + c)) : 0.0;
+                for (int q = 0; q < 4; ++q) v[j][q] = 0.0;
+            } else if (!transpose) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const double2 p = __ldcg(reinterpret_cast<const double2 *>(T + (size_t)r * kOzNb + oz_col(lane, 2 * h)));
+                    v[j][2 * h] = p.x;
+                    v[j][2 * h + 1] = p.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[j][q] = __ldcg(T + (size_t)oz_col(lane, q) * kOzNb + r);
             }
         }
 #pragma unroll

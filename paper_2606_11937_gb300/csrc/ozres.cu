@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) ozr_split_a_kernel(const double *A, int64
     for (int r = warp; r < 64; r += 8) {
         double v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = T[r * P + lane + 32 * q];
+        for (int q = 0; q < 4; ++q) v[q] = T[r * P + oz_col(lane, q)];
         const int row = hb * 64 + r;
         const int e = ozaki_split_row(v, out + (size_t)row * kOzNb, (size_t)kOzNb * kOzNb, false);
         if (lane == 0) expA[t * kOzNb + row] = e;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) ozr_split_x_kernel(const double *X, int64
     double v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int64_t i = J * kOzNb + lane + 32 * q;
+        const int64_t i = J * kOzNb + oz_col(lane, q);
         v[q] = (col < nrhs && i < n) ? X[col * ldx + i] : 0.0;
     }
     uint16_t *out = reinterpret_cast<uint16_t *>(slices) + ((size_t)chJ * kOzS * kOzrCols + c) * kOzNb;
