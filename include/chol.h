@@ -79,7 +79,10 @@ typedef enum {
     CHOL_SCHED_AUTO = 0,            /* autotuner choice (or dataflow if untuned) */
     CHOL_SCHED_FORK_JOIN = 1,       /* per step J: POTRF, TRSM grid, collapsed SYRK+GEMM grid */
     CHOL_SCHED_FORK_JOIN_NAIVE = 2, /* as above, update grid over block rows only */
-    CHOL_SCHED_DATAFLOW = 3         /* one persistent kernel, dependency counters */
+    CHOL_SCHED_DATAFLOW = 3,        /* one persistent kernel, dependency counters */
+    CHOL_SCHED_LEFT_LOOKING = 4     /* the left-looking variant (Section 3.1): per block column K, one
+                                       CTA per tile (I, K) applies all its updates J < K, then POTRF,
+                                       then the TRSM grid; same per-tile update order, same bits */
 } chol_schedule;
 
 /* opts->flags */
@@ -87,7 +90,8 @@ enum {
     CHOL_FLAG_NOOP = 1,          /* replace every tile kernel body by a no-op (Section 4.2 overhead runs) */
     CHOL_FLAG_PRIORITY = 2,      /* dataflow: POTRF, TRSM, SYRK and the GEMMs updating the next 16 panel columns
                                     before the other GEMMs (OpenMP 4.5 priorities analog) */
-    CHOL_FLAG_GRAPH = 4,         /* fork-join: replay the per-step launches from a cached CUDA graph */
+    CHOL_FLAG_GRAPH = 4,         /* launch-ordered schedules: capture the launches into a CUDA graph and
+                                    launch it as one unit (the call then waits for it) */
     CHOL_FLAG_TEST_WITHHOLD = 8, /* dataflow test hook: never release the last POTRF, so the
                                     bounded waits must expire with CHOL_ERR_TIMEOUT */
     CHOL_FLAG_FP64_TC = 16,      /* FP64: run SYRK/GEMM on the bf16 tensor cores with binary64

@@ -272,36 +272,111 @@ __global__ void __launch_bounds__(Body::kBlock) fj_update_naive_kernel(const __g
     Body::cta_fini(g, sm);
 }
 
+// left-looking: for block column K one CTA per tile (I, K), I >= K, applies
+// all of the tile's updates J = 0 .. K-1 in ascending order (SYRK for I == K)
+template <class Body>
+__global__ void __launch_bounds__(Body::kBlock) fj_left_update_kernel(const __grid_constant__ typename Body::Args g,
+                                                             SchedArgs a, int K) {
+    typename Body::Smem &sm = body_smem<Body>();
+    if (ld_acquire_s32(&a.ctl->abort)) return;
+    const int I = K + (int)blockIdx.x;
+    Body::cta_init(g, sm);
+    for (int J = 0; J < K; ++J) Body::run(g, a, 0, I, K, J, sm);
+    Body::cta_fini(g, sm);
+}
+
+// The launch-ordered schedules: right-looking fork-join (collapsed update
+// grid, or one CTA per block row) and left-looking.
+enum FjVariant : int { FJ_COLLAPSED = 0, FJ_NAIVE = 1, FJ_LEFT = 2 };
+
+inline int fj_variant(int sched) {
+    return sched == CHOL_SCHED_FORK_JOIN_NAIVE ? FJ_NAIVE : sched == CHOL_SCHED_LEFT_LOOKING ? FJ_LEFT : FJ_COLLAPSED;
+}
+
 template <class Body, typename KernelT>
 int set_smem_attr(KernelT kernel) {
     CHOL_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)body_smem_bytes<Body>()));
     return CHOL_OK;
 }
 
+// Issue the launches of a launch-ordered schedule on st; returns their count.
 template <class Body>
-int run_fork_join(const typename Body::Args &g, const SchedArgs &a, int M, bool naive, cudaStream_t st,
-                  int *launches) {
-    int rc;
-    if ((rc = set_smem_attr<Body>(fj_potrf_kernel<Body>)) || (rc = set_smem_attr<Body>(fj_trsm_kernel<Body>)) ||
-        (rc = set_smem_attr<Body>(fj_update_kernel<Body>)) || (rc = set_smem_attr<Body>(fj_update_naive_kernel<Body>)))
-        return rc;
+int fj_issue(const typename Body::Args &g, const SchedArgs &a, int M, int variant, cudaStream_t st) {
     const size_t smem = body_smem_bytes<Body>();
     int L = 0;
+    if (variant == FJ_LEFT) {
+        // per block column K: the updates from the left, POTRF, the TRSM grid
+        for (int K = 0; K < M; ++K) {
+            if (K > 0) {
+                fj_left_update_kernel<Body><<<M - K, Body::kBlock, smem, st>>>(g, a, K);
+                ++L;
+            }
+            fj_potrf_kernel<Body><<<1, Body::kBlock, smem, st>>>(g, a, K);
+            ++L;
+            if (M - K - 1 > 0) {
+                fj_trsm_kernel<Body><<<M - K - 1, Body::kBlock, smem, st>>>(g, a, K);
+                ++L;
+            }
+        }
+        return L;
+    }
     for (int J = 0; J < M; ++J) {
         fj_potrf_kernel<Body><<<1, Body::kBlock, smem, st>>>(g, a, J);
         ++L;
         const int rest = M - J - 1;
         if (rest > 0) {
             fj_trsm_kernel<Body><<<rest, Body::kBlock, smem, st>>>(g, a, J);
-            if (naive)
+            if (variant == FJ_NAIVE)
                 fj_update_naive_kernel<Body><<<rest, Body::kBlock, smem, st>>>(g, a, J);
             else
                 fj_update_kernel<Body><<<(unsigned)((int64_t)rest * (rest + 1) / 2), Body::kBlock, smem, st>>>(g, a, J);
             L += 2;
         }
     }
+    return L;
+}
+
+// Launch-ordered schedule (variant: FJ_*).  e0 (may be null) is recorded on st
+// right before the first kernel.  With CHOL_FLAG_GRAPH the launches are
+// captured into a CUDA graph, which is instantiated and then launched as one
+// unit (the host's launch latency leaves the critical path); the call then
+// waits for the graph before destroying it.
+template <class Body>
+int run_fork_join(const typename Body::Args &g, const SchedArgs &a, int M, int variant, cudaStream_t st,
+                  int *launches, cudaEvent_t e0) {
+    int rc;
+    if ((rc = set_smem_attr<Body>(fj_potrf_kernel<Body>)) || (rc = set_smem_attr<Body>(fj_trsm_kernel<Body>)) ||
+        (rc = set_smem_attr<Body>(fj_update_kernel<Body>)) || (rc = set_smem_attr<Body>(fj_update_naive_kernel<Body>)) ||
+        (rc = set_smem_attr<Body>(fj_left_update_kernel<Body>)))
+        return rc;
+    if (!(a.flags & CHOL_FLAG_GRAPH)) {
+        if (e0) CHOL_CUDA(cudaEventRecord(e0, st));
+        *launches = fj_issue<Body>(g, a, M, variant, st);
+        CHOL_CUDA(cudaGetLastError());
+        return CHOL_OK;
+    }
+    // captured on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); nothing runs during the capture
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    CHOL_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t ec = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    int L = 0;
+    if (ec == cudaSuccess) {
+        L = fj_issue<Body>(g, a, M, variant, cs);
+        ec = cudaStreamEndCapture(cs, &graph);
+    }
+    cudaStreamDestroy(cs);
+    if (ec != cudaSuccess) return cuda_fail(ec, "fork-join graph capture", __FILE__, __LINE__);
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess && e0) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "fork-join graph", __FILE__, __LINE__);
     *launches = L;
-    CHOL_CUDA(cudaGetLastError());
     return CHOL_OK;
 }
 
@@ -658,9 +733,10 @@ int launch_dataflow(const typename Body::Args &g, const SchedArgs &a, DFArgs d, 
 
 // single-matrix FP64 / FP32 helpers used by factor.cu
 template <typename T>
-int run_fork_join(const TileStore<T> &S, const SchedArgs &a, bool naive, cudaStream_t st, int *launches) {
+int run_fork_join(const TileStore<T> &S, const SchedArgs &a, int variant, cudaStream_t st, int *launches,
+                  cudaEvent_t e0) {
     typename SimtBody<T>::Args g{S};
-    return run_fork_join<SimtBody<T>>(g, a, S.M, naive, st, launches);
+    return run_fork_join<SimtBody<T>>(g, a, S.M, variant, st, launches, e0);
 }
 
 template <typename T>

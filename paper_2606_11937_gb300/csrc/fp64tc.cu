@@ -332,8 +332,7 @@ int fp64tc_schedule(double *store, int64_t n, Control *ctl, unsigned long long *
             d.num_matrices = 1;
             rc = launch_dataflow<OzBody>(g, a, d, o, st, launches, e0);
         } else {
-            if (e0) cudaEventRecord(e0, st);
-            rc = run_fork_join<OzBody>(g, a, (int)M, sched == CHOL_SCHED_FORK_JOIN_NAIVE, st, launches);
+            rc = run_fork_join<OzBody>(g, a, (int)M, fj_variant(sched), st, launches, e0);
         }
     }
     cudaFreeAsync(ws, st);

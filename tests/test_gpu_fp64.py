@@ -16,7 +16,7 @@ from paper_facts import task_counts
 
 pytestmark = pytest.mark.gpu
 
-SCHEDS = ["dataflow", "fork_join", "fork_join_naive"]
+SCHEDS = ["dataflow", "fork_join", "fork_join_naive", "left_looking"]
 
 
 @pytest.mark.parametrize("sched", SCHEDS)
@@ -79,6 +79,33 @@ def test_schedules_bitwise_equal_with_priority(nb):
             L, info, st, rc = gpu_factor(A, schedule="dataflow", nb=nb, flags=flags, num_ctas=ctas)
             assert rc == 0 and info == 0
             assert np.array_equal(L, ref)
+
+
+@pytest.mark.parametrize("sched", ["fork_join", "fork_join_naive", "left_looking"])
+def test_graph_replay_same_bits(sched):
+    """CHOL_FLAG_GRAPH: the launch-ordered schedules captured into a CUDA graph
+    give the bits of the direct launches, with the same launch count."""
+    import paper_2606_11937_gb300 as chol
+    A = matrix("se", 1000, 6, 1e-2)
+    L0, info0, st0, rc0 = gpu_factor(A, schedule=sched, nb=64)
+    L1, info1, st1, rc1 = gpu_factor(A, schedule=sched, nb=64, flags=chol.CHOL_FLAG_GRAPH)
+    assert rc0 == rc1 == 0 and info0 == info1 == 0
+    assert np.array_equal(L0, L1)
+    assert st0.launches == st1.launches
+    assert tuple(st1.tasks) == task_counts(16)
+
+
+def test_left_looking_launch_count():
+    """Left-looking: per block column K an update launch (K > 0), the POTRF and
+    the TRSM grid (K < M - 1): 3M - 2 schedule launches, as many as the
+    right-looking fork-join (POTRF, TRSM grid, update grid per step J < M - 1,
+    and the last POTRF); the same bits."""
+    A = matrix("gram", 1024, 2)
+    L, info, st, rc = gpu_factor(A, schedule="left_looking", nb=128)
+    Lr, info_r, st_r, rc_r = gpu_factor(A, schedule="fork_join", nb=128)
+    assert rc == rc_r == 0 and info == info_r == 0
+    assert st.launches == st_r.launches
+    assert np.array_equal(L, Lr)
 
 
 def test_non_spd_info():
