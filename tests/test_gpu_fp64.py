@@ -258,6 +258,28 @@ def test_trace_respects_dependencies():
                 assert ev[nd][1] <= t0, ((ty, I, K, J), nd)
 
 
+def test_solve_exact_integer_factor():
+    """L0 with diagonal in {1, 2, 4} and small integer entries, x integer, b = A x:
+    every intermediate of both sweeps is an integer, so the solve must return x
+    exactly.  The diagonal blocks of L0 are ill-conditioned (kappa_inf about
+    1e12), so this also runs the substitution the solve keeps for them."""
+    import torch
+
+    import paper_2606_11937_gb300 as chol
+    import seeded_inputs as si
+    n = 1000
+    A, L0 = si.exact_integer_factor(n, seed=31)
+    r = si.rng(32)
+    X0 = r.integers(-3, 4, size=(n, 5)).astype(np.float64)
+    B = A @ X0
+    assert np.max(np.abs(B)) < 2.0 ** 50
+    dL = chol.colmajor(L0)
+    dB = chol.colmajor(B)
+    chol.chol_solve_ex(dL, dB)
+    torch.cuda.synchronize()
+    assert np.array_equal(dB.cpu().numpy(), X0)
+
+
 @pytest.mark.parametrize("n,nrhs", [(2048, 1), (1000, 16), (777, 37), (64, 3), (1, 1)])
 def test_solve_fp64(n, nrhs):
     import torch
