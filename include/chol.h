@@ -80,9 +80,13 @@ typedef enum {
     CHOL_SCHED_FORK_JOIN = 1,       /* per step J: POTRF, TRSM grid, collapsed SYRK+GEMM grid */
     CHOL_SCHED_FORK_JOIN_NAIVE = 2, /* as above, update grid over block rows only */
     CHOL_SCHED_DATAFLOW = 3,        /* one persistent kernel, dependency counters */
-    CHOL_SCHED_LEFT_LOOKING = 4     /* the left-looking variant (Section 3.1): per block column K, one
+    CHOL_SCHED_LEFT_LOOKING = 4,    /* the left-looking variant (Section 3.1): per block column K, one
                                        CTA per tile (I, K) applies all its updates J < K, then POTRF,
                                        then the TRSM grid; same per-tile update order, same bits */
+    CHOL_SCHED_TOP_LOOKING = 5      /* the top-looking variant (Section 3.1): block row I in one launch,
+                                       one CTA per tile (I, K) applying its updates as the row's tiles
+                                       to its left become final, then its TRSM (POTRF for K = I);
+                                       same per-tile update order, same bits */
 } chol_schedule;
 
 /* opts->flags */

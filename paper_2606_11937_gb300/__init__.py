@@ -24,14 +24,14 @@ CHOL_OK, CHOL_ERR_ARG, CHOL_ERR_NOT_SPD, CHOL_ERR_NOMEM, CHOL_ERR_CUDA = 0, -1, 
 CHOL_ERR_TIMEOUT, CHOL_ERR_NOT_CONVERGED, CHOL_ERR_BUSY, CHOL_ERR_HANDLE, CHOL_ERR_UNSUPPORTED = -5, -6, -7, -8, -9
 CHOL_FP64, CHOL_FP32, CHOL_TF32, CHOL_BF16, CHOL_FP16 = 0, 1, 2, 3, 4
 CHOL_SCHED_AUTO, CHOL_SCHED_FORK_JOIN, CHOL_SCHED_FORK_JOIN_NAIVE, CHOL_SCHED_DATAFLOW = 0, 1, 2, 3
-CHOL_SCHED_LEFT_LOOKING = 4
+CHOL_SCHED_LEFT_LOOKING, CHOL_SCHED_TOP_LOOKING = 4, 5
 CHOL_FLAG_NOOP, CHOL_FLAG_PRIORITY, CHOL_FLAG_GRAPH, CHOL_FLAG_TEST_WITHHOLD, CHOL_FLAG_FP64_TC = 1, 2, 4, 8, 16
 CHOL_FLAG_GMRES_IR = 32
 
 PRECISIONS = {"fp64": CHOL_FP64, "fp32": CHOL_FP32, "tf32": CHOL_TF32, "bf16": CHOL_BF16, "fp16": CHOL_FP16}
 SCHEDULES = {"auto": CHOL_SCHED_AUTO, "fork_join": CHOL_SCHED_FORK_JOIN,
              "fork_join_naive": CHOL_SCHED_FORK_JOIN_NAIVE, "dataflow": CHOL_SCHED_DATAFLOW,
-             "left_looking": CHOL_SCHED_LEFT_LOOKING}
+             "left_looking": CHOL_SCHED_LEFT_LOOKING, "top_looking": CHOL_SCHED_TOP_LOOKING}
 
 _i32, _i64, _dbl, _vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
 

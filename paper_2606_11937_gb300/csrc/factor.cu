@@ -39,7 +39,7 @@ static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o
                      int64_t *info, chol_stats *stats, double *A_out, int64_t lda_out) {
     const int64_t M = (n + nb - 1) / nb;
     const int sched = o.schedule == CHOL_SCHED_AUTO ? CHOL_SCHED_DATAFLOW : o.schedule;
-    CHOL_CHECK_ARG(sched >= CHOL_SCHED_FORK_JOIN && sched <= CHOL_SCHED_LEFT_LOOKING, "unknown schedule");
+    CHOL_CHECK_ARG(sched >= CHOL_SCHED_FORK_JOIN && sched <= CHOL_SCHED_TOP_LOOKING, "unknown schedule");
     cudaStream_t st = (cudaStream_t)o.stream;
     const int64_t ntasks = num_tasks(M);
     const size_t ctl_bytes = align256(sizeof(Control));
@@ -68,7 +68,7 @@ static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o
         } else if (sched == CHOL_SCHED_DATAFLOW) {
             rc = run_dataflow<double>(S, a, ws.queue, ws.deps, o, st, &launches, e0);
         } else {
-            rc = run_fork_join<double>(S, a, fj_variant(sched), st, &launches, e0);
+            rc = run_fork_join<double>(S, a, fj_variant(sched), st, &launches, e0, o.timeout_s);
         }
         if (rc != CHOL_OK) break;
         cudaEventRecord(e1, st);

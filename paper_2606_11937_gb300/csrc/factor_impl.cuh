@@ -285,12 +285,65 @@ __global__ void __launch_bounds__(Body::kBlock) fj_left_update_kernel(const __gr
     Body::cta_fini(g, sm);
 }
 
+// top-looking: block row I in one launch of I + 1 CTAs.  A CTA takes a ticket
+// (the row's tiles K = 0 .. I in ticket order), applies the updates J < K of
+// tile (I, K) as the tiles (I, J) of the same row become final (their flag
+// reaches the row's epoch I + 1, acquire), then its TRSM (or, for K = I, the
+// POTRF), and publishes its own flag (release).  A CTA only waits for tiles
+// of earlier tickets, whose CTAs are already resident, so the waits end
+// whatever the residency (the tensor-memory bodies hold a whole SM's shared
+// memory, so no CTA's tensor-memory allocation waits for another CTA of the
+// launch); each wait is bounded by the timeout (CHOL_ERR_TIMEOUT).
+template <class Body>
+__global__ void __launch_bounds__(Body::kBlock) fj_top_row_kernel(const __grid_constant__ typename Body::Args g,
+                                                         SchedArgs a, int I, int32_t *fin, uint64_t timeout_ns) {
+    typename Body::Smem &sm = body_smem<Body>();
+    __shared__ int s_k, s_ok;
+    if (threadIdx.x == 0) {
+        s_k = (int)(atomicAdd(&a.ctl->ticket, 1ull) - (unsigned long long)I * (I + 1) / 2);
+        s_ok = 1;
+    }
+    __syncthreads();
+    const int K = s_k;
+    if (ld_acquire_s32(&a.ctl->abort)) return;
+    Body::cta_init(g, sm);
+    const uint64_t deadline = global_ns() + timeout_ns;
+    for (int J = 0; J < K; ++J) {
+        if (threadIdx.x == 0) {
+            while (ld_acquire_s32(fin + J) != I + 1) {
+                if (ld_relaxed_s32(&a.ctl->abort)) {
+                    s_ok = 0;
+                    break;
+                }
+                if (global_ns() > deadline) {
+                    if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 30;
+                    st_release_s32(&a.ctl->abort, 1);
+                    s_ok = 0;
+                    break;
+                }
+                nanosleep_ns(256);
+            }
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        Body::run(g, a, 0, I, K, J, sm);  // GEMM (K < I) or SYRK (K == I)
+    }
+    if (s_ok) Body::run(g, a, 0, I, K, K, sm);  // TRSM (K < I) or POTRF (K == I)
+    __syncthreads();
+    // the barrier orders every thread's stores of the tile before the release
+    if (threadIdx.x == 0 && s_ok) st_release_s32(fin + K, I + 1);
+    Body::cta_fini(g, sm);
+}
+
 // The launch-ordered schedules: right-looking fork-join (collapsed update
-// grid, or one CTA per block row) and left-looking.
-enum FjVariant : int { FJ_COLLAPSED = 0, FJ_NAIVE = 1, FJ_LEFT = 2 };
+// grid, or one CTA per block row), left-looking, top-looking.
+enum FjVariant : int { FJ_COLLAPSED = 0, FJ_NAIVE = 1, FJ_LEFT = 2, FJ_TOP = 3 };
 
 inline int fj_variant(int sched) {
-    return sched == CHOL_SCHED_FORK_JOIN_NAIVE ? FJ_NAIVE : sched == CHOL_SCHED_LEFT_LOOKING ? FJ_LEFT : FJ_COLLAPSED;
+    return sched == CHOL_SCHED_FORK_JOIN_NAIVE ? FJ_NAIVE
+           : sched == CHOL_SCHED_LEFT_LOOKING  ? FJ_LEFT
+           : sched == CHOL_SCHED_TOP_LOOKING   ? FJ_TOP
+                                               : FJ_COLLAPSED;
 }
 
 template <class Body, typename KernelT>
@@ -301,9 +354,14 @@ int set_smem_attr(KernelT kernel) {
 
 // Issue the launches of a launch-ordered schedule on st; returns their count.
 template <class Body>
-int fj_issue(const typename Body::Args &g, const SchedArgs &a, int M, int variant, cudaStream_t st) {
+int fj_issue(const typename Body::Args &g, const SchedArgs &a, int M, int variant, cudaStream_t st, int32_t *fin,
+             uint64_t timeout_ns) {
     const size_t smem = body_smem_bytes<Body>();
     int L = 0;
+    if (variant == FJ_TOP) {
+        for (int I = 0; I < M; ++I) fj_top_row_kernel<Body><<<I + 1, Body::kBlock, smem, st>>>(g, a, I, fin, timeout_ns);
+        return M;
+    }
     if (variant == FJ_LEFT) {
         // per block column K: the updates from the left, POTRF, the TRSM grid
         for (int K = 0; K < M; ++K) {
@@ -343,15 +401,29 @@ int fj_issue(const typename Body::Args &g, const SchedArgs &a, int M, int varian
 // waits for the graph before destroying it.
 template <class Body>
 int run_fork_join(const typename Body::Args &g, const SchedArgs &a, int M, int variant, cudaStream_t st,
-                  int *launches, cudaEvent_t e0) {
+                  int *launches, cudaEvent_t e0, double timeout_s) {
     int rc;
     if ((rc = set_smem_attr<Body>(fj_potrf_kernel<Body>)) || (rc = set_smem_attr<Body>(fj_trsm_kernel<Body>)) ||
         (rc = set_smem_attr<Body>(fj_update_kernel<Body>)) || (rc = set_smem_attr<Body>(fj_update_naive_kernel<Body>)) ||
-        (rc = set_smem_attr<Body>(fj_left_update_kernel<Body>)))
+        (rc = set_smem_attr<Body>(fj_left_update_kernel<Body>)) || (rc = set_smem_attr<Body>(fj_top_row_kernel<Body>)))
         return rc;
+    const uint64_t tns = (uint64_t)(timeout_s * 1e9);
+    // top-looking: one "final" flag per tile of the current block row (epoch I + 1)
+    int32_t *fin = nullptr;
+    if (variant == FJ_TOP) {
+        CHOL_CUDA(cudaMallocAsync(&fin, (size_t)M * 4, st));
+        CHOL_CUDA(cudaMemsetAsync(fin, 0, (size_t)M * 4, st));
+    }
+    struct FinFree {
+        int32_t *p;
+        cudaStream_t s;
+        ~FinFree() {
+            if (p) cudaFreeAsync(p, s);
+        }
+    } fin_free{fin, st};
     if (!(a.flags & CHOL_FLAG_GRAPH)) {
         if (e0) CHOL_CUDA(cudaEventRecord(e0, st));
-        *launches = fj_issue<Body>(g, a, M, variant, st);
+        *launches = fj_issue<Body>(g, a, M, variant, st, fin, tns);
         CHOL_CUDA(cudaGetLastError());
         return CHOL_OK;
     }
@@ -364,7 +436,7 @@ int run_fork_join(const typename Body::Args &g, const SchedArgs &a, int M, int v
     cudaError_t ec = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     int L = 0;
     if (ec == cudaSuccess) {
-        L = fj_issue<Body>(g, a, M, variant, cs);
+        L = fj_issue<Body>(g, a, M, variant, cs, fin, tns);
         ec = cudaStreamEndCapture(cs, &graph);
     }
     cudaStreamDestroy(cs);
@@ -734,9 +806,9 @@ int launch_dataflow(const typename Body::Args &g, const SchedArgs &a, DFArgs d, 
 // single-matrix FP64 / FP32 helpers used by factor.cu
 template <typename T>
 int run_fork_join(const TileStore<T> &S, const SchedArgs &a, int variant, cudaStream_t st, int *launches,
-                  cudaEvent_t e0) {
+                  cudaEvent_t e0, double timeout_s) {
     typename SimtBody<T>::Args g{S};
-    return run_fork_join<SimtBody<T>>(g, a, S.M, variant, st, launches, e0);
+    return run_fork_join<SimtBody<T>>(g, a, S.M, variant, st, launches, e0, timeout_s);
 }
 
 template <typename T>

@@ -332,7 +332,7 @@ int fp64tc_schedule(double *store, int64_t n, Control *ctl, unsigned long long *
             d.num_matrices = 1;
             rc = launch_dataflow<OzBody>(g, a, d, o, st, launches, e0);
         } else {
-            rc = run_fork_join<OzBody>(g, a, (int)M, fj_variant(sched), st, launches, e0);
+            rc = run_fork_join<OzBody>(g, a, (int)M, fj_variant(sched), st, launches, e0, o.timeout_s);
         }
     }
     cudaFreeAsync(ws, st);

@@ -482,7 +482,7 @@ static int mixed_factor_impl(int64_t n, const double *A, int64_t lda, const chol
     const int64_t M = (n + nb - 1) / nb;
     CHOL_CHECK_ARG(M < 65536 && num_tiles(M) * nb < (1ll << 31), "matrix too large for the operand maps");
     const int sched = o.schedule == CHOL_SCHED_AUTO ? CHOL_SCHED_DATAFLOW : o.schedule;
-    CHOL_CHECK_ARG(sched >= CHOL_SCHED_FORK_JOIN && sched <= CHOL_SCHED_LEFT_LOOKING, "unknown schedule");
+    CHOL_CHECK_ARG(sched >= CHOL_SCHED_FORK_JOIN && sched <= CHOL_SCHED_TOP_LOOKING, "unknown schedule");
     cudaStream_t st = (cudaStream_t)o.stream;
     prepare_pool();
     const int fmt = op_fmt(o.precision);
@@ -552,7 +552,7 @@ static int mixed_factor_impl(int64_t n, const double *A, int64_t lda, const chol
             oo.num_ctas = grid;
             rc = launch_dataflow<MixedBody>(g, a, d, oo, st, &launches, e0);
         } else {
-            rc = run_fork_join<MixedBody>(g, a, (int)M, fj_variant(sched), st, &launches, e0);
+            rc = run_fork_join<MixedBody>(g, a, (int)M, fj_variant(sched), st, &launches, e0, o.timeout_s);
         }
         if (rc != CHOL_OK) break;
         cudaEventRecord(e1, st);

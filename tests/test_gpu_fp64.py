@@ -16,7 +16,7 @@ from paper_facts import task_counts
 
 pytestmark = pytest.mark.gpu
 
-SCHEDS = ["dataflow", "fork_join", "fork_join_naive", "left_looking"]
+SCHEDS = ["dataflow", "fork_join", "fork_join_naive", "left_looking", "top_looking"]
 
 
 @pytest.mark.parametrize("sched", SCHEDS)
@@ -81,7 +81,7 @@ def test_schedules_bitwise_equal_with_priority(nb):
             assert np.array_equal(L, ref)
 
 
-@pytest.mark.parametrize("sched", ["fork_join", "fork_join_naive", "left_looking"])
+@pytest.mark.parametrize("sched", ["fork_join", "fork_join_naive", "left_looking", "top_looking"])
 def test_graph_replay_same_bits(sched):
     """CHOL_FLAG_GRAPH: the launch-ordered schedules captured into a CUDA graph
     give the bits of the direct launches, with the same launch count."""

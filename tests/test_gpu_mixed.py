@@ -55,7 +55,7 @@ def test_mixed_factor_error_and_schedules(prec):
     A = matrix("gram", n, 0)
     Lref, _ = oracle_factor("gram", n, 0)
     outs = []
-    for sched in ("dataflow", "fork_join", "fork_join_naive", "left_looking"):
+    for sched in ("dataflow", "fork_join", "fork_join_naive", "left_looking", "top_looking"):
         rc, h, dA = mixed(A, prec, sched, 128)
         assert rc == 0 and h.info == 0
         st = chol.chol_mixed_last_stats()
