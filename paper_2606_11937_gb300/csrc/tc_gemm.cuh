@@ -141,14 +141,18 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint
 constexpr int kTcStages = 3;
 constexpr int kBoxRows = 128;              // rows per TMA box
 constexpr int kBoxBytes = kBoxRows * 128;  // 128 bytes of K per row
-constexpr int kStageBytes = 4 * kBoxBytes; // up to 2 A boxes + 2 B boxes
+constexpr int kStageBytes = 4 * kBoxBytes; // up to 2 A boxes + 2 B boxes (or A hi/lo + B hi/lo)
+// The staging area (kTcStages x kStageBytes) is cut into ring slots of the
+// size one K-chunk of the update needs: 3 slots of 4 boxes, or 6 of 2 boxes
+// (tile order 128, one product), so more loads are in flight.
+constexpr int kTcMaxSlots = 6;
 
 // Operand formats of the mixed precisions
 enum OpFmt : int32_t { OP_F16 = 0, OP_BF16 = 1, OP_TF32 = 2 };
 
 struct TcShared {
-    uint64_t full[kTcStages];
-    uint64_t empty[kTcStages];
+    uint64_t full[kTcMaxSlots];
+    uint64_t empty[kTcMaxSlots];
     uint64_t acc_full[2];   // per accumulator buffer (two when a sub-tile takes <= 256 columns)
     uint64_t tmem_empty[2];
     uint64_t drain;
@@ -178,7 +182,7 @@ struct TcGemmArgs {
 // One CTA (256 threads) initialises its barriers and allocates 512 TMEM columns.
 __device__ inline void tc_cta_init(TcShared &ts) {
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < kTcMaxSlots; ++s) {
             mbar_init(&ts.full[s], 1);
             mbar_init(&ts.empty[s], 1);
         }
@@ -320,7 +324,14 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
     const int cols = MH * NN;                  // tensor-memory columns of a sub-tile
     const int nsr = nb / SR, nsc = nb / NN;
     const int kchunks = nb / (g.tf32 ? 32 : 64);
-    const uint32_t stage_bytes = (uint32_t)(MH + NN / 128) * kBoxBytes;
+    // the three products hi.hi, hi.lo, lo.hi of a tile of order 128 read one
+    // K-chunk of A hi, A lo, B hi and B lo from one slot (each box loaded once)
+    const bool fused = g.passes == 3 && MH == 1 && NN == 128;
+    const int boxes = fused ? 4 : MH + NN / 128;
+    const uint32_t stage_bytes = (uint32_t)boxes * kBoxBytes;
+    const int nst_fit = (kTcStages * kStageBytes) / (int)stage_bytes;
+    const uint32_t nst = (uint32_t)(nst_fit < kTcMaxSlots ? nst_fit : kTcMaxSlots);  // ring slots
+    const int npass = fused ? 1 : g.passes;  // loads per K-chunk: per product, or once
     const uint32_t ring0 = ts.ring, acc0 = ts.acc_uses;
     const uint64_t deadline = global_ns() + timeout_ns;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -329,7 +340,7 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
     int nsub = 0;
     for (int ri = 0; ri < nsr; ++ri)
         for (int ci = 0; ci < nsc; ++ci) nsub += skip(ri, ci) ? 0 : 1;
-    const uint32_t iters_per_sub = (uint32_t)(g.passes * kchunks);
+    const uint32_t iters_per_sub = (uint32_t)(npass * kchunks);
     const bool defer = defer_last && nsub == 1 && cols <= 256;
 
     if (warp == 0 && lane == 0) {
@@ -339,17 +350,25 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
         for (int ri = 0; ri < nsr && !tc_failed(ts); ++ri)
             for (int ci = 0; ci < nsc && !tc_failed(ts); ++ci) {
                 if (skip(ri, ci)) continue;
-                for (int p = 0; p < g.passes && !tc_failed(ts); ++p)
+                for (int p = 0; p < npass && !tc_failed(ts); ++p)
                     for (int kc = 0; kc < kchunks; ++kc, ++f) {
-                        const int s = (int)(f % kTcStages);
-                        if (f >= (uint32_t)kTcStages &&
-                            !mbar_wait(&ts.empty[s], ((f / kTcStages) & 1) ^ 1, deadline)) {
+                        const int s = (int)(f % nst);
+                        if (f >= nst && !mbar_wait(&ts.empty[s], ((f / nst) & 1) ^ 1, deadline)) {
                             *(volatile int32_t *)&ts.fail = 1;
                             break;
                         }
                         mbar_arrive_expect_tx(&ts.full[s], stage_bytes);
-                        const uint32_t dst = smem_u32(stages + (size_t)s * kStageBytes);
+                        const uint32_t dst = smem_u32(stages + (size_t)s * stage_bytes);
                         const int x = kc * (g.tf32 ? 32 : 64);
+                        if (fused) {
+                            // A hi, A lo, B hi, B lo (products 0 and 2 name the A maps, 0 and 1 the B maps)
+                            const int ar = aRow0 + ri * SR, br = bRow0 + ci * NN;
+                            tma_load_2d(dst, g.mapA[0], &ts.full[s], x, ar);
+                            tma_load_2d(dst + kBoxBytes, g.mapA[2], &ts.full[s], x, ar);
+                            tma_load_2d(dst + 2 * kBoxBytes, g.mapB[0], &ts.full[s], x, br);
+                            tma_load_2d(dst + 3 * kBoxBytes, g.mapB[1], &ts.full[s], x, br);
+                            continue;
+                        }
                         for (int h = 0; h < MH; ++h)
                             tma_load_2d(dst + h * kBoxBytes, g.mapA[p], &ts.full[s], x, aRow0 + ri * SR + h * 128);
                         for (int q = 0; q < NN / 128; ++q)
@@ -372,15 +391,32 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
                 tc_fence_after();
                 const uint32_t tcol = b * (uint32_t)cols;
                 bool first = true;
-                for (int p = 0; p < g.passes && !tc_failed(ts); ++p)
+                for (int p = 0; p < npass && !tc_failed(ts); ++p)
                     for (int kc = 0; kc < kchunks; ++kc, ++f) {
-                        const int s = (int)(f % kTcStages);
-                        if (!mbar_wait(&ts.full[s], (f / kTcStages) & 1, deadline)) {
+                        const int s = (int)(f % nst);
+                        if (!mbar_wait(&ts.full[s], (f / nst) & 1, deadline)) {
                             *(volatile int32_t *)&ts.fail = 1;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t base = smem_u32(stages + (size_t)s * kStageBytes);
+                        const uint32_t base = smem_u32(stages + (size_t)s * stage_bytes);
+                        if (fused) {
+                            // hi.hi + hi.lo + lo.hi per K step (tf32, tile order 128)
+                            const uint32_t d = ts.tmem_base + tcol;
+#pragma unroll
+                            for (int k4 = 0; k4 < 4; ++k4) {
+                                const uint64_t ahi = sdesc_sw128(base + k4 * 32);
+                                const uint64_t alo = sdesc_sw128(base + kBoxBytes + k4 * 32);
+                                const uint64_t bhi = sdesc_sw128(base + 2 * kBoxBytes + k4 * 32);
+                                const uint64_t blo = sdesc_sw128(base + 3 * kBoxBytes + k4 * 32);
+                                tc_mma<true>(d, ahi, bhi, g.idesc, first ? 0u : 1u);
+                                tc_mma<true>(d, ahi, blo, g.idesc, 1u);
+                                tc_mma<true>(d, alo, bhi, g.idesc, 1u);
+                                first = false;
+                            }
+                            tc_commit(&ts.empty[s]);
+                            continue;
+                        }
 #pragma unroll
                         for (int k4 = 0; k4 < 4; ++k4) {
                             const uint64_t bdesc = sdesc_sw128(base + MH * kBoxBytes + k4 * 32);
