@@ -103,6 +103,7 @@ struct MixedSmem {
 };
 static_assert(sizeof(SimtSmem<double>) <= sizeof(MixedSmem::stages), "SIMT scratch must fit in the stage area");
 static_assert(kPotrf128SmemBytes <= sizeof(MixedSmem::stages), "the shared-memory POTRF must fit in the stage area");
+static_assert(2 * 128 * 129 * sizeof(float) <= sizeof(MixedSmem::stages), "the shared-memory TRSM must fit in the stage area");
 
 __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
     uint32_t r;
@@ -112,10 +113,17 @@ __device__ __forceinline__ uint32_t f32_to_tf32(float x) {
 
 __device__ __forceinline__ float pow2f(int e) { return ldexpf(1.0f, e); }
 
-// CTA-wide max of |x| over a tile of nb*nb floats
+// CTA-wide max of |x| over a tile of nb*nb floats (count a multiple of 4,
+// T 16-byte aligned: float4 loads, four in flight per thread)
 __device__ float tile_absmax(const float *T, int64_t count, float *red) {
     float m = 0.f;
-    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) m = fmaxf(m, fabsf(__ldcg(T + i)));
+    const float4 *T4 = reinterpret_cast<const float4 *>(T);
+    const int64_t n4 = count / 4;
+#pragma unroll 4
+    for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) {
+        const float4 v = __ldcg(T4 + i);
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x / 32] = m;
     __syncthreads();
@@ -140,32 +148,124 @@ __device__ __forceinline__ int scale_exponent(float mx) {
 }
 
 // Write the tensor-core operand copies of tile t (binary32 values in T).
+// Four consecutive elements per thread and step (16-byte loads, several in
+// flight: the tile was just written by this CTA and is read back from L2).
 __device__ void write_operands(const MixedArgs &g, int64_t t, const float *T, float *red) {
     const int nb = g.S.nb;
-    const int64_t cnt = (int64_t)nb * nb;
+    const int64_t cnt = (int64_t)nb * nb, n4 = cnt / 4;
     const size_t off = (size_t)t * cnt;
+    const float4 *T4 = reinterpret_cast<const float4 *>(T);
     if (g.fmt == OP_TF32) {
-        uint32_t *hi = reinterpret_cast<uint32_t *>(g.op_hi) + off;
-        uint32_t *lo = g.op_lo ? reinterpret_cast<uint32_t *>(g.op_lo) + off : nullptr;
-        for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-            const float x = __ldcg(T + i);
-            const uint32_t h = f32_to_tf32(x);
+        uint4 *hi = reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(g.op_hi) + off);
+        uint4 *lo = g.op_lo ? reinterpret_cast<uint4 *>(reinterpret_cast<uint32_t *>(g.op_lo) + off) : nullptr;
+#pragma unroll 4
+        for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) {
+            const float4 x = __ldcg(T4 + i);
+            const uint4 h = make_uint4(f32_to_tf32(x.x), f32_to_tf32(x.y), f32_to_tf32(x.z), f32_to_tf32(x.w));
             hi[i] = h;
-            if (lo) lo[i] = f32_to_tf32(x - __uint_as_float(h));
+            if (lo)
+                lo[i] = make_uint4(f32_to_tf32(x.x - __uint_as_float(h.x)), f32_to_tf32(x.y - __uint_as_float(h.y)),
+                                   f32_to_tf32(x.z - __uint_as_float(h.z)), f32_to_tf32(x.w - __uint_as_float(h.w)));
         }
     } else {
         const int e = scale_exponent(tile_absmax(T, cnt, red));
         const float s = pow2f(e);
         if (threadIdx.x == 0) g.exps[t] = e;
         if (g.fmt == OP_BF16) {
-            __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(g.op_hi) + off;
-            for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) o[i] = __float2bfloat16_rn(__ldcg(T + i) * s);
+            __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(reinterpret_cast<__nv_bfloat16 *>(g.op_hi) + off);
+#pragma unroll 4
+            for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) {
+                const float4 x = __ldcg(T4 + i);
+                o[2 * i] = __floats2bfloat162_rn(x.x * s, x.y * s);
+                o[2 * i + 1] = __floats2bfloat162_rn(x.z * s, x.w * s);
+            }
         } else {
-            __half *o = reinterpret_cast<__half *>(g.op_hi) + off;
-            for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) o[i] = __float2half_rn(__ldcg(T + i) * s);
+            __half2 *o = reinterpret_cast<__half2 *>(reinterpret_cast<__half *>(g.op_hi) + off);
+#pragma unroll 4
+            for (int64_t i = threadIdx.x; i < n4; i += blockDim.x) {
+                const float4 x = __ldcg(T4 + i);
+                o[2 * i] = __floats2half2_rn(x.x * s, x.y * s);
+                o[2 * i + 1] = __floats2half2_rn(x.z * s, x.w * s);
+            }
         }
     }
     fence_proxy_async_global();  // make the generic-proxy writes visible to later TMA reads
+    __syncthreads();
+}
+
+// TRSM of a tile of order 128 in binary32 with both tiles in shared memory:
+// B <- B L^{-T} (row-major tiles), right-looking over panels of 16 columns.
+// A panel is solved row by row (thread r owns row r; x_c = (b_c - sum over
+// k < c of x_k L(c, k)) / L(c, c), the division a multiplication by the
+// reciprocal), then applied to the columns right of it as one rank-16 update
+// by the 256 threads, each holding an 8-row x (up to 7)-column block of
+// accumulators.  The solved tile is stored back and left in shared memory
+// (Bs, padded rows) for the operand copies.  smem: 2 x 128 x 129 floats.
+constexpr int kTrsmP = 129;
+__device__ void smem_trsm128_f32(float *B, const float *L, float *smem) {
+    constexpr int N = 128, P = kTrsmP, W = 16;
+    float *Bs = smem, *Ls = smem + N * P;
+    __shared__ float rinv[N];
+    const int t = threadIdx.x;
+    for (int e = t; e < N * N / 4; e += blockDim.x) {
+        const int r = (4 * e) / N, c = (4 * e) % N;
+        const float4 b = __ldcg(reinterpret_cast<const float4 *>(B) + e);
+        const float4 l = __ldcg(reinterpret_cast<const float4 *>(L) + e);
+        Bs[r * P + c] = b.x; Bs[r * P + c + 1] = b.y; Bs[r * P + c + 2] = b.z; Bs[r * P + c + 3] = b.w;
+        Ls[r * P + c] = l.x; Ls[r * P + c + 1] = l.y; Ls[r * P + c + 2] = l.z; Ls[r * P + c + 3] = l.w;
+    }
+    __syncthreads();
+    if (t < N) rinv[t] = 1.0f / Ls[t * P + t];
+    __syncthreads();
+    const int tx = t & 15, ty = t >> 4;
+    for (int jb = 0; jb < N; jb += W) {
+        if (t < N) {
+            float x[W];
+#pragma unroll
+            for (int c = 0; c < W; ++c) x[c] = Bs[t * P + jb + c];
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                float v = x[c];
+#pragma unroll
+                for (int k = 0; k < c; ++k) v = fmaf(-x[k], Ls[(jb + c) * P + jb + k], v);
+                x[c] = v * rinv[jb + c];
+            }
+#pragma unroll
+            for (int c = 0; c < W; ++c) Bs[t * P + jb + c] = x[c];
+        }
+        __syncthreads();
+        const int c0 = jb + W, nj = (N - c0) / 16;  // column blocks of 16 right of the panel
+        if (nj > 0) {
+            float acc[8][7];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 7; ++j) acc[i][j] = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < W; ++k) {
+                float a[8], b[7];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a[i] = Bs[(ty * 8 + i) * P + jb + k];
+#pragma unroll
+                for (int j = 0; j < 7; ++j) b[j] = j < nj ? Ls[(c0 + tx + 16 * j) * P + jb + k] : 0.f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 7; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 7; ++j)
+                    if (j < nj) Bs[(ty * 8 + i) * P + c0 + tx + 16 * j] -= acc[i][j];
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < N * N / 4; e += blockDim.x) {
+        const int r = (4 * e) / N, c = (4 * e) % N;
+        reinterpret_cast<float4 *>(B)[e] =
+            make_float4(Bs[r * P + c], Bs[r * P + c + 1], Bs[r * P + c + 2], Bs[r * P + c + 3]);
+    }
     __syncthreads();
 }
 
@@ -238,9 +338,13 @@ struct MixedBody {
                 }
             } break;
             case T_TRSM: {
-                SimtSmem<float> &ss = *reinterpret_cast<SimtSmem<float> *>(sm.stages);
                 float *B = g.S.tile(I, J);
-                tile_trsm<float>(B, g.S.tile(J, J), nb, ss);
+                if (nb == 128) {
+                    smem_trsm128_f32(B, g.S.tile(J, J), reinterpret_cast<float *>(sm.stages));
+                } else {
+                    SimtSmem<float> &ss = *reinterpret_cast<SimtSmem<float> *>(sm.stages);
+                    tile_trsm<float>(B, g.S.tile(J, J), nb, ss);
+                }
                 write_operands(g, tile_index(I, J), B, reinterpret_cast<float *>(sm.stages));
             } break;
             default: {
