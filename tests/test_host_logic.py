@@ -41,6 +41,19 @@ def test_binding_signatures_cover_the_header():
     assert not missing, missing
 
 
+def test_binding_constants_match_the_header():
+    """Every enumerator the header assigns (statuses, precisions, schedules,
+    flags) has the same value in the Python binding."""
+    import paper_2606_11937_gb300 as chol
+    txt = open(os.path.join(ROOT, "include", "chol.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    found = dict((m.group(1), int(m.group(2))) for m in re.finditer(r"\b(CHOL_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt))
+    assert len(found) >= 25
+    for name, value in found.items():
+        assert hasattr(chol, name), name
+        assert getattr(chol, name) == value, (name, getattr(chol, name), value)
+
+
 def test_shard_partitions_exactly():
     import bench_batched
     for count in (0, 1, 7, 4096, 4097):
