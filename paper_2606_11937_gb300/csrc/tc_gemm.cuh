@@ -253,16 +253,18 @@ __device__ inline bool tc_epilogue_sub(TcShared &ts, float *xpose, float *C, int
     for (int h = 0; h < MH; ++h) {
         const int row0 = ri * SR + h * 128 + q * 32;
         for (int c = 0; c < NN; c += 32) {
+            // the 32 rows of C this chunk updates are requested first, so their
+            // L2 latency overlaps the tensor-memory load and the transpose
+            float *cb = C + (size_t)row0 * nb + ci * NN + c + lane;
+            float cv[32];
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) cv[rr] = __ldcg(cb + (size_t)rr * nb);
             uint32_t r[32];
             tmem_ld32(ts.tmem_base + ((uint32_t)(q * 32) << 16) + tcol + (uint32_t)(h * NN + c), r);
             tmem_ld_wait();
 #pragma unroll
             for (int j = 0; j < 32; ++j) xp[j * 32 + (lane ^ j)] = (__uint_as_float(r[j]) * sa) * sb;
             __syncwarp();
-            float *cb = C + (size_t)row0 * nb + ci * NN + c + lane;
-            float cv[32];
-#pragma unroll
-            for (int rr = 0; rr < 32; ++rr) cv[rr] = __ldcg(cb + (size_t)rr * nb);
 #pragma unroll
             for (int rr = 0; rr < 32; ++rr) cb[(size_t)rr * nb] = cv[rr] - xp[lane * 32 + (rr ^ lane)];
             __syncwarp();
