@@ -151,6 +151,30 @@ def test_gmres_refinement(prec, nugget):
     assert np.max(np.abs(X - Xref)) <= max(1e-12, 10 * kappa_u) * np.max(np.abs(Xref))
 
 
+@pytest.mark.parametrize("flags", [0, 32])
+def test_refinement_many_columns_and_a_zero_column(flags):
+    """20 right-hand sides (two 16-column chunks of the tensor-core residual),
+    one of them zero: classic and GMRES-based refinement reach 1e-14 on every
+    column (oracle), and the zero column's solution is exactly zero."""
+    import torch
+
+    import paper_2606_11937_gb300 as chol
+    n = 1300
+    A = matrix("se", n, 2, 1e-2)
+    B = si.rhs(n, 20, seed=9)
+    B[:, 7] = 0.0
+    rc, h, dA = mixed(A, "tf32", "dataflow", 128, max_iter=40, flags=flags)
+    assert rc == 0 and h.info == 0
+    rc, dX, iters, berr = h.solve(chol.colmajor(B), raise_on_error=False)
+    torch.cuda.synchronize()
+    X = dX.cpu().numpy()
+    h.close()
+    print(f"flags {flags}: rc {rc} iterations {iters} berr {berr:.2e}")
+    assert rc == 0 and berr <= 1e-14
+    assert oracle.backward_error(A, X, B) <= 1e-14
+    assert np.all(X[:, 7] == 0.0)
+
+
 def test_mixed_non_spd_info():
     n = 1024
     A = matrix("gram", n, 4).copy()
