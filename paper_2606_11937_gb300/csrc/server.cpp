@@ -71,10 +71,11 @@ size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 int64_t tasks_of(int64_t M) { return M * (M + 1) * (M + 2) / 6; }
 
 // FP64 requests of order above this factor with SYRK/GEMM/TRSM on the tensor
-// cores (binary64 accuracy, tiles of 128); smaller ones on the FP64 pipe,
-// where the shorter critical path wins.  A pure function of n, so a request
-// gives the same bits alone and in a mix.
-constexpr int64_t kServeTcMinN = 4096;
+// cores (binary64 accuracy, tiles of 128); smaller ones on the FP64 pipe.
+// Measured single factorizations (dataflow): n = 1024 3.5 ms on both engines,
+// n = 1536 5.5 against 8.2 ms, n = 4096 15.6 against 31.5 ms.  A pure function
+// of n, so a request gives the same bits alone and in a mix.
+constexpr int64_t kServeTcMinN = 1024;
 bool fp64_on_tensor_cores(int64_t n) { return n > kServeTcMinN; }
 int64_t fp64_nb(int64_t n) { return fp64_on_tensor_cores(n) ? 128 : chol_default_nb(n, CHOL_FP64); }
 

@@ -24,7 +24,7 @@ def test_served_results_same_alone_and_in_mix():
     import torch
 
     import paper_2606_11937_gb300 as chol
-    # 5000: an FP64 request large enough for the tensor-core engine
+    # 1500, 2048, 5000: FP64 requests on the tensor-core engine (order above 1024)
     sizes = [300, 1500, 64, 777, 2048, 129, 1024, 500, 5000]
     precs = ["fp64", "fp32", "fp64", "bf16", "fp64", "tf32", "fp64", "fp16", "fp64"]
     mats = [si.gram_plus_identity(n, 200 + i) if i % 2 == 0 else si.se_covariance(n, 300 + i, nugget=1e-1)
