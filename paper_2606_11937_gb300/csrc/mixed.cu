@@ -553,6 +553,17 @@ struct chol_factor_s {
 constexpr int64_t kOzrMinN = 1024;
 
 namespace chol {
+// Device bytes a mixed handle of order n keeps for the tensor-core residual
+// once it has solved (the slices of A), and the per-solve workspace of that
+// residual; 0 where the binary64 CUDA-core residual is used.  (The serving
+// layer's memory budget.)
+size_t mixed_residual_keep_bytes(int64_t n) { return n >= kOzrMinN && ozr_supported(n) ? ozr_a_bytes(n) : 0; }
+size_t mixed_residual_ws_bytes(int64_t n, int64_t nrhs) {
+    return n >= kOzrMinN && ozr_supported(n) ? (ozr_ws_bytes(n, nrhs, num_sms()) + 255) / 256 * 256 : 0;
+}
+}  // namespace chol
+
+namespace chol {
 
 // Residual R = B - A X of the refinement (B null: R = -A X): on the tensor
 // cores with binary64 accuracy (ozres.cu) when the handle holds the slices of

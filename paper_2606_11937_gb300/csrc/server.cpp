@@ -33,6 +33,8 @@ int fp64_solve_store(const double *store, int64_t n, int64_t nb, double *X, int6
                      cudaStream_t st, double timeout_s);
 size_t fp64_store_bytes(int64_t n, int64_t nb);
 size_t fp64tc_extra_bytes(int64_t n);
+size_t mixed_residual_keep_bytes(int64_t n);
+size_t mixed_residual_ws_bytes(int64_t n, int64_t nrhs);
 }  // namespace chol
 
 using Clock = std::chrono::steady_clock;
@@ -89,18 +91,22 @@ size_t need_bytes(const chol_request &r, bool reuse) {
         return chol::fp64_store_bytes(n, nb) + a256((size_t)tasks_of(M) * 20 + 1024) + a256(solve_ws) +
                (fp64_on_tensor_cores(n) ? chol::fp64tc_extra_bytes(n) : 0);
     }
-    const size_t ir = a256((size_t)n * nrhs * 12 + (size_t)n * 8 + 3 * (size_t)nrhs * 8 + 1024) + a256(solve_ws);
+    // refinement workspace, including the tensor-core residual's (its slices of
+    // A are counted with the kept factor: the handle holds them once built)
+    const size_t ir = a256((size_t)n * nrhs * 12 + (size_t)n * 8 + 3 * (size_t)nrhs * 8 + 1024) + a256(solve_ws) +
+                      chol::mixed_residual_ws_bytes(n, nrhs);
     if (reuse) return ir;
     const int64_t nb = chol_default_nb(n, r.precision), M = (n + nb - 1) / nb;
     const size_t tiles = (size_t)M * (M + 1) / 2, te = (size_t)nb * nb;
     const size_t per = r.precision == CHOL_FP32 ? 12 : (r.precision == CHOL_TF32 ? 8 : 6);
-    return tiles * te * per + 160 * te * 8 + (size_t)tasks_of(M) * 20 + ir + 4096;
+    return tiles * te * per + 160 * te * 8 + (size_t)tasks_of(M) * 20 + ir + 4096 +
+           chol::mixed_residual_keep_bytes(n);
 }
 
 size_t keep_bytes_of(const chol_request &r) {
     if (r.precision == CHOL_FP64) return chol::fp64_store_bytes(r.n, fp64_nb(r.n));
     const int64_t nb = chol_default_nb(r.n, r.precision), M = (r.n + nb - 1) / nb;
-    return a256((size_t)M * (M + 1) / 2 * nb * nb * 4);
+    return a256((size_t)M * (M + 1) / 2 * nb * nb * 4) + chol::mixed_residual_keep_bytes(r.n);
 }
 
 }  // namespace
