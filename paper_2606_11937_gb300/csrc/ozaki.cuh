@@ -224,6 +224,22 @@ __device__ __forceinline__ double int_scaled_fast(long long x, int scale) {
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+// L2 policy that makes the lines it touches the first to be evicted: the C
+// tiles stream through L2 once per update, the slices of a block column are
+// reused by many updates
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void cp_async16_hint(uint32_t dst, const void *src, uint64_t pol) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_f64x2_hint(double *p, double2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
 }
@@ -288,10 +304,11 @@ __device__ inline bool oz_epilogue_quarter(OzSmem &sm, double *C, int qq, uint32
     // stage this warp's 32 x 16 block of C in shared memory (async, coalesced
     // 16-byte copies) while the accumulators are produced
     double *cblk = C + (size_t)(q * 32) * kOzNb + col0;
+    const uint64_t pol = l2_evict_first();
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int idx = i * 32 + lane, rr = idx >> 3, seg = idx & 7;
-        cp_async16(smem_u32(xp + xp_idx(rr, 2 * seg)), cblk + (size_t)rr * kOzNb + 2 * seg);
+        cp_async16_hint(smem_u32(xp + xp_idx(rr, 2 * seg)), cblk + (size_t)rr * kOzNb + 2 * seg, pol);
     }
     // one lane polls, the others wait at the shuffle
     bool got = true;
@@ -361,7 +378,7 @@ __device__ inline bool oz_epilogue_quarter(OzSmem &sm, double *C, int qq, uint32
     for (int i = 0; i < 8; ++i) {
         const int idx = i * 32 + lane, rr = idx >> 3, seg = idx & 7;
         const double2 v = *reinterpret_cast<const double2 *>(xp + xp_idx(rr, 2 * seg));
-        *reinterpret_cast<double2 *>(cblk + (size_t)rr * kOzNb + 2 * seg) = v;
+        st_f64x2_hint(cblk + (size_t)rr * kOzNb + 2 * seg, v, pol);
     }
     __syncwarp();
     return true;
