@@ -289,11 +289,11 @@ def run_fp64(args, world, rank, local):
         peak = bf16 / 36.0
         # DRAM bytes (read + write) of one df_kernel<OzBody> launch at the
         # default configuration (n = 32768, nb = 128, dataflow + priority),
-        # from one single-pass ncu capture of this kernel (1.260 TB read,
-        # 0.369 TB written); only for that configuration
+        # from one single-pass ncu capture of this kernel (1.180 TB read,
+        # 0.361 TB written); only for that configuration
         default_cfg = (args.n == 32768 and nb == 128 and args.schedule == "dataflow" and args.flags == 18
                        and args.num_ctas == 0)
-        traffic = 1.630e12 if default_cfg else None
+        traffic = 1.541e12 if default_cfg else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "df_kernel<OzBody>" if args.schedule == "dataflow" else "fork-join kernels",
                 "peak_source": f"measured sustained bf16 {bf16} TFLOP/s / 36 slice products (FP64-equivalent)",
