@@ -77,64 +77,93 @@ __device__ __forceinline__ void tile_of(int64_t t, int &I, int &K) {
 
 // Column-major lower(A) -> row-major tiles; entries outside the n x n matrix
 // are the identity; the strict upper triangle of diagonal tiles is set to 0
-// (A's upper triangle is never read).  grid.x = tile, grid.y = 32 x 32 sub-block.
+// (A's upper triangle is never read).  grid.x = tile, grid.y = (32-row strip,
+// group of kRpW 32-column blocks): each thread moves 4 kRpW elements, all of
+// its loads in flight before the transposes through shared memory.
+constexpr int kRpW = 4;
+
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) repack_kernel(const Tin *A, int64_t lda, int64_t n, Tout *store,
                                                      int nb, int64_t tile0) {
-    __shared__ Tout buf[32][33];
+    __shared__ Tout buf[kRpW][32][33];
     int I, K;
     const int64_t t = tile0 + blockIdx.x;
     tile_of(t, I, K);
-    const int nsb = (nb + 31) / 32;
-    const int sr = blockIdx.y / nsb, sc = blockIdx.y % nsb;
+    const int nsb = (nb + 31) / 32, ngr = (nsb + kRpW - 1) / kRpW;
+    const int sr = blockIdx.y / ngr, sc0 = (blockIdx.y % ngr) * kRpW;
     Tout *tile = store + (size_t)t * nb * nb;
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
-        const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
-        Tout v = Tout(0);
-        if (r < nb && c < nb) {
-            if (i < n && j < n) v = j <= i ? (Tout)A[j * lda + i] : Tout(0);
-            else v = i == j ? Tout(1) : Tout(0);
+#pragma unroll
+    for (int w = 0; w < kRpW; ++w) {
+        const int sc = sc0 + w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int yy = threadIdx.y + 8 * q;
+            const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
+            const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
+            Tout v = Tout(0);
+            if (sc < nsb && r < nb && c < nb) {
+                if (i < n && j < n) v = j <= i ? (Tout)A[j * lda + i] : Tout(0);
+                else v = i == j ? Tout(1) : Tout(0);
+            }
+            buf[w][yy][threadIdx.x] = v;
         }
-        buf[yy][threadIdx.x] = v;
     }
     __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
-        if (r < nb && c < nb) tile[(size_t)r * nb + c] = buf[threadIdx.x][yy];
+#pragma unroll
+    for (int w = 0; w < kRpW; ++w) {
+        const int sc = sc0 + w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int yy = threadIdx.y + 8 * q;
+            const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
+            if (sc < nsb && r < nb && c < nb) tile[(size_t)r * nb + c] = buf[w][threadIdx.x][yy];
+        }
     }
 }
 
-// Row-major tiles -> lower triangle of column-major A (i >= j, i, j < n).
+// Row-major tiles -> lower triangle of column-major A (i >= j, i, j < n);
+// the same blocking as repack_kernel.
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(256) unpack_kernel(const Tin *store, int nb, Tout *A, int64_t lda, int64_t n,
                                                      int64_t tile0) {
-    __shared__ Tin buf[32][33];
+    __shared__ Tin buf[kRpW][32][33];
     int I, K;
     const int64_t t = tile0 + blockIdx.x;
     tile_of(t, I, K);
-    const int nsb = (nb + 31) / 32;
-    const int sr = blockIdx.y / nsb, sc = blockIdx.y % nsb;
+    const int nsb = (nb + 31) / 32, ngr = (nsb + kRpW - 1) / kRpW;
+    const int sr = blockIdx.y / ngr, sc0 = (blockIdx.y % ngr) * kRpW;
     const Tin *tile = store + (size_t)t * nb * nb;
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
-        buf[yy][threadIdx.x] = (r < nb && c < nb) ? tile[(size_t)r * nb + c] : Tin(0);
+#pragma unroll
+    for (int w = 0; w < kRpW; ++w) {
+        const int sc = sc0 + w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int yy = threadIdx.y + 8 * q;
+            const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
+            buf[w][yy][threadIdx.x] = (sc < nsb && r < nb && c < nb) ? tile[(size_t)r * nb + c] : Tin(0);
+        }
     }
     __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
-        const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
-        if (r < nb && c < nb && i < n && j < n && j <= i) A[j * lda + i] = (Tout)buf[threadIdx.x][yy];
+#pragma unroll
+    for (int w = 0; w < kRpW; ++w) {
+        const int sc = sc0 + w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int yy = threadIdx.y + 8 * q;
+            const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
+            const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
+            if (sc < nsb && r < nb && c < nb && i < n && j < n && j <= i) A[j * lda + i] = (Tout)buf[w][threadIdx.x][yy];
+        }
     }
 }
 
 template <typename Tin, typename Tout>
 int launch_repack(const Tin *A, int64_t lda, int64_t n, Tout *store, int nb, int64_t M, cudaStream_t st) {
-    const int nsb = (nb + 31) / 32;
+    const int nsb = (nb + 31) / 32, ngr = (nsb + kRpW - 1) / kRpW;
     const int64_t tiles = num_tiles(M);
     for (int64_t t0 = 0; t0 < tiles; t0 += 1ll << 30) {
         const int64_t cnt = tiles - t0 < (1ll << 30) ? tiles - t0 : (1ll << 30);
-        repack_kernel<Tin, Tout><<<dim3((unsigned)cnt, nsb * nsb), dim3(32, 8), 0, st>>>(A, lda, n, store, nb, t0);
+        repack_kernel<Tin, Tout><<<dim3((unsigned)cnt, nsb * ngr), dim3(32, 8), 0, st>>>(A, lda, n, store, nb, t0);
     }
     CHOL_CUDA(cudaGetLastError());
     return CHOL_OK;
@@ -142,11 +171,11 @@ int launch_repack(const Tin *A, int64_t lda, int64_t n, Tout *store, int nb, int
 
 template <typename Tin, typename Tout>
 int launch_unpack(const Tin *store, int nb, int64_t M, Tout *A, int64_t lda, int64_t n, cudaStream_t st) {
-    const int nsb = (nb + 31) / 32;
+    const int nsb = (nb + 31) / 32, ngr = (nsb + kRpW - 1) / kRpW;
     const int64_t tiles = num_tiles(M);
     for (int64_t t0 = 0; t0 < tiles; t0 += 1ll << 30) {
         const int64_t cnt = tiles - t0 < (1ll << 30) ? tiles - t0 : (1ll << 30);
-        unpack_kernel<Tin, Tout><<<dim3((unsigned)cnt, nsb * nsb), dim3(32, 8), 0, st>>>(store, nb, A, lda, n, t0);
+        unpack_kernel<Tin, Tout><<<dim3((unsigned)cnt, nsb * ngr), dim3(32, 8), 0, st>>>(store, nb, A, lda, n, t0);
     }
     CHOL_CUDA(cudaGetLastError());
     return CHOL_OK;
