@@ -169,8 +169,12 @@ int64_t chol_last_info(void);
 int chol_factor_ex(int64_t n, double *A, int64_t lda, const chol_opts *opts,
                    int64_t *info, chol_stats *stats);
 
-/* As chol_factor_ex, but A is a HOST buffer: the library copies it to the
- * device, factors it and copies the lower triangle back (end-to-end path). */
+/* As chol_factor_ex, but A is a HOST buffer (pinned memory copies fastest):
+ * the library copies the lower triangle to the device, factors it and copies
+ * the lower triangle back (end-to-end path).  Each copy moves, per block of
+ * 512 columns starting at column j0, rows j0 .. n-1 of those columns: the
+ * lower triangle plus the upper part of each block's diagonal square, which
+ * is written back unchanged. */
 int chol_factor_host(int64_t n, double *A_host, int64_t lda, const chol_opts *opts,
                      int64_t *info, chol_stats *stats);
 

@@ -201,15 +201,28 @@ int chol_factor_host(int64_t n, double *A_host, int64_t lda, const chol_opts *op
     double *dA = nullptr;
     CHOL_CUDA(cudaMallocAsync(&dA, (size_t)n * n * sizeof(double), st));
     int rc = CHOL_OK;
+    // only the lower triangle travels: per block of kCopyCols columns, rows
+    // j0 .. n-1 (the few entries above the diagonal inside a block's diagonal
+    // square come along; the factorization never reads them, and on the way
+    // back they are the caller's own values)
+    constexpr int64_t kCopyCols = 512;
+    auto copy_lower = [&](double *dst, int64_t ldd, const double *src, int64_t lds, cudaMemcpyKind kind) {
+        for (int64_t j0 = 0; j0 < n; j0 += kCopyCols) {
+            const int64_t w = n - j0 < kCopyCols ? n - j0 : kCopyCols;
+            const cudaError_t e = cudaMemcpy2DAsync(dst + j0 * ldd + j0, ldd * sizeof(double), src + j0 * lds + j0,
+                                                    lds * sizeof(double), (size_t)(n - j0) * sizeof(double), (size_t)w,
+                                                    kind, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
     do {
-        if (cudaMemcpy2DAsync(dA, n * sizeof(double), A_host, lda * sizeof(double), n * sizeof(double), n,
-                              cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        if (copy_lower(dA, n, A_host, lda, cudaMemcpyHostToDevice) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "H2D", __FILE__, __LINE__);
             break;
         }
         if ((rc = chol_factor_ex(n, dA, n, &o, info, stats)) != CHOL_OK) break;
-        if (cudaMemcpy2DAsync(A_host, lda * sizeof(double), dA, n * sizeof(double), n * sizeof(double), n,
-                              cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        if (copy_lower(A_host, lda, dA, n, cudaMemcpyDeviceToHost) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "D2H", __FILE__, __LINE__);
             break;
         }

@@ -183,18 +183,26 @@ def test_chol_factor_plain_entry():
     assert chol.chol_last_info() == 11
 
 
-def test_host_buffer_entry():
+@pytest.mark.parametrize("n,lda", [(513, 513), (1300, 1310)])
+def test_host_buffer_entry(n, lda):
+    """Host buffer in and out (only the lower triangle travels, in blocks of
+    512 columns): the factor in the lower triangle, the strict upper triangle
+    and the padding rows beyond n exactly as they were."""
     import torch
 
     import paper_2606_11937_gb300 as chol
-    n = 513
     A = matrix("gram", n, 9)
     Lref, _ = oracle_factor("gram", n, 9)
-    h = torch.empty_strided((n, n), (1, n), dtype=torch.float64, pin_memory=True)
-    h.copy_(torch.from_numpy(A))
-    info, st = chol.chol_factor_host(h, chol.opts(nb=64, schedule="dataflow"))
+    h = torch.full((n, lda), -7.25, dtype=torch.float64).pin_memory()  # column j at h[j, :]
+    hv = h.T  # lda x n column-major view
+    hv[:n, :] = torch.from_numpy(A)
+    before = hv.clone()
+    info, st = chol.chol_factor_host(hv, chol.opts(nb=64, schedule="dataflow"), n=n, lda=lda)
     assert info == 0
-    assert scaled_error(h.numpy(), Lref, A) <= TOL_SCALED
+    out = hv.numpy()
+    assert scaled_error(out[:n, :n], Lref, A) <= TOL_SCALED
+    assert np.array_equal(np.triu(out[:n, :n], 1), np.triu(before.numpy()[:n, :n], 1))
+    assert np.array_equal(out[n:, :], before.numpy()[n:, :])
 
 
 def test_noop_mode_runs_the_task_graph():
