@@ -17,7 +17,9 @@
 // barriers).  It stores the result and releases its own flag.
 // Every wait is bounded by a %globaltimer deadline after which the kernel
 // records CHOL_ERR_TIMEOUT and returns.  grid.y splits the right-hand sides
-// into slices of kRC columns, each with its own tickets and flags.
+// into slices of RC columns (16, or 4 when there are at most 4, so a thread
+// works on one row instead of four and no arithmetic goes to empty columns),
+// each slice with its own tickets and flags.
 #pragma once
 
 #include "common.cuh"
@@ -25,7 +27,10 @@
 namespace chol {
 
 constexpr int kSB = 64;  // row block of the solve
-constexpr int kRC = 16;  // right-hand-side columns per CTA
+constexpr int kRC = 16;  // right-hand-side columns per CTA (the binary64 residual kernel's slices too)
+
+// columns per slice of a solve with nrhs right-hand sides
+inline int solve_rc(int64_t nrhs) { return nrhs <= 4 ? 4 : kRC; }
 
 // Factor accessors: element (i, j), i >= j, of L.
 // block(r0, c0) gives the address of element (r0, c0) of a 64 x 64 block that
@@ -72,12 +77,12 @@ struct SolveCtl {
 
 constexpr double kSolveKappa = 65536.0;  // largest kappa_inf of a diagonal block applied by its inverse
 
-template <typename T>
+template <typename T, int RC = kRC>
 struct SolveSmem {
     T Ls[kSB][kSB + 1];   // off-diagonal block being applied (first the diagonal block)
     T W[kSB][kSB + 1];    // inverse of the diagonal block, or the block itself (substitution)
     T rinv[kSB];          // reciprocals of the diagonal block's diagonal
-    T Xs[kSB][kRC + 1];
+    T Xs[kSB][RC + 1];
     T nrm[2][2];          // per warp of the first two: max row sums of |L_II| and |W|
     int I;
     int known;            // leading blocks of the sweep known to be finished
@@ -139,9 +144,13 @@ __device__ __forceinline__ void store_block_regs(const T (&v)[kBlkPer], T (*S)[k
 // L_II y = x (forward) or L_II^T y = x (backward).  Warp w owns columns 2w
 // and 2w+1; lane l owns rows l and l+32 and receives each solved entry by a
 // shuffle, so the 64 steps need no block barrier.  Ends with a barrier.
-template <typename T, bool FWD>
-__device__ void diag_solve(SolveSmem<T> &sm, const T (*Ld)[kSB + 1]) {
+template <typename T, bool FWD, int RC>
+__device__ void diag_solve(SolveSmem<T, RC> &sm, const T (*Ld)[kSB + 1]) {
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (warp >= RC / 2) {  // no columns for this warp
+        __syncthreads();
+        return;
+    }
     const int c0 = 2 * warp, c1 = 2 * warp + 1;
     T a0 = sm.Xs[lane][c0], a1 = sm.Xs[lane][c1], b0 = sm.Xs[lane + 32][c0], b1 = sm.Xs[lane + 32][c1];
 #pragma unroll 4
@@ -192,10 +201,13 @@ __device__ __forceinline__ bool wait_flag(const int32_t *flag, uint64_t deadline
 // blocks from the last, block I gets -L(J, I)^T x_J for J > I.  The u-th update
 // of a CTA uses block J(u) = u (forward) or nblk - 1 - u (backward), which the
 // sweep finishes in that same order.
-template <typename T, class Acc, bool FWD>
+template <typename T, class Acc, bool FWD, int RC>
 __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t ldb, int64_t n, int64_t nrhs,
                                                           int32_t *flags, SolveCtl *ctl, uint64_t timeout_ns) {
-    __shared__ SolveSmem<T> sm;
+    static_assert(RC == 4 || RC == 16, "slices of 4 or 16 columns");
+    constexpr int RS = 256 / RC;        // row stride of a thread's rows
+    constexpr int RPT = kSB / RS;       // rows per thread (4 for RC = 16, 1 for RC = 4)
+    __shared__ SolveSmem<T, RC> sm;
     const int nblk = (int)((n + kSB - 1) / kSB);
     const int y = blockIdx.y;
     if (threadIdx.x == 0) {
@@ -208,8 +220,8 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
     const int I = FWD ? t : nblk - 1 - t;
     const int nupd = t;
     auto Jof = [&](int u) { return FWD ? u : nblk - 1 - u; };
-    const int64_t c0 = (int64_t)y * kRC;
-    const int c = threadIdx.x % kRC, rq = threadIdx.x / kRC;  // rows rq + 16 q
+    const int64_t c0 = (int64_t)y * RC;
+    const int c = threadIdx.x % RC, rq = threadIdx.x / RC;  // rows rq + RS q
     int32_t *fl = flags + (size_t)y * nblk;
     const uint64_t deadline = global_ns() + timeout_ns;
     const int64_t rI = (int64_t)I * kSB;
@@ -224,10 +236,10 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
         load_block_regs<T>(L, n, rI, rI, true, dr);
         store_block_regs<T, Acc>(dr, sm.Ls, false);
     }
-    T acc[4];
+    T acc[RPT];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int64_t i = rI + rq + 16 * q;
+    for (int q = 0; q < RPT; ++q) {
+        const int64_t i = rI + rq + RS * q;
         acc[q] = (i < n && c0 + c < nrhs) ? B[(c0 + c) * ldb + i] : T(0);
     }
     __syncthreads();
@@ -271,7 +283,7 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
         if (threadIdx.x == 0) sm.subst = subst;
     }
     // solution values of the next finished block, prefetched into registers
-    constexpr int kXPer = kSB * kRC / 256;
+    constexpr int kXPer = kSB * RC / 256;
     T xr[kXPer];
     bool xpre = false;
     for (int u = 0; u < nupd; ++u) {
@@ -295,7 +307,7 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
         const int64_t rJ = (int64_t)J * kSB;
 #pragma unroll
         for (int q = 0; q < kXPer; ++q) {
-            const int e = threadIdx.x + 256 * q, k = e / kRC, cc = e % kRC;
+            const int e = threadIdx.x + 256 * q, k = e / RC, cc = e % RC;
             if (!xpre) {
                 const int64_t i = rJ + k;
                 xr[q] = (i < n && c0 + cc < nrhs) ? __ldcg(B + (c0 + cc) * ldb + i) : T(0);
@@ -309,7 +321,7 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
             if (xpre) {
 #pragma unroll
                 for (int q = 0; q < kXPer; ++q) {
-                    const int e = threadIdx.x + 256 * q, k = e / kRC, cc = e % kRC;
+                    const int e = threadIdx.x + 256 * q, k = e / RC, cc = e % RC;
                     const int64_t i = rN + k;
                     xr[q] = (i < n && c0 + cc < nrhs) ? __ldcg(B + (c0 + cc) * ldb + i) : T(0);
                 }
@@ -320,35 +332,37 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
         for (int k = 0; k < kSB; ++k) {
             const T xk = sm.Xs[k][c];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fma(-sm.Ls[rq + 16 * q][k], xk, acc[q]);
+            for (int q = 0; q < RPT; ++q) acc[q] = fma(-sm.Ls[rq + RS * q][k], xk, acc[q]);
         }
     }
     __syncthreads();
     // diagonal block: L_II y = acc (forward) or L_II^T x = acc (backward)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sm.Xs[rq + 16 * q][c] = acc[q];
+    for (int q = 0; q < RPT; ++q) sm.Xs[rq + RS * q][c] = acc[q];
     __syncthreads();
     if (!sm.subst) {
         // y = W acc (forward), x = W^T acc (backward); W is zero above its diagonal
-        T y[4] = {T(0), T(0), T(0), T(0)};
+        T y[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) y[q] = T(0);
 #pragma unroll 8
         for (int k = 0; k < kSB; ++k) {
             const T xk = sm.Xs[k][c];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = rq + 16 * q;
+            for (int q = 0; q < RPT; ++q) {
+                const int r = rq + RS * q;
                 y[q] = fma(FWD ? sm.W[r][k] : sm.W[k][r], xk, y[q]);
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) sm.Xs[rq + 16 * q][c] = y[q];
+        for (int q = 0; q < RPT; ++q) sm.Xs[rq + RS * q][c] = y[q];
         __syncthreads();
     } else {
-        diag_solve<T, FWD>(sm, sm.W);
+        diag_solve<T, FWD, RC>(sm, sm.W);
     }
-    for (int e = threadIdx.x; e < kSB * kRC; e += blockDim.x) {
-        const int k = e / kRC, cc = e % kRC;
+    for (int e = threadIdx.x; e < kSB * RC; e += blockDim.x) {
+        const int k = e / RC, cc = e % RC;
         const int64_t i = rI + k;
         if (i < n && c0 + cc < nrhs) B[(c0 + cc) * ldb + i] = sm.Xs[k][cc];
     }
@@ -359,7 +373,8 @@ __global__ void __launch_bounds__(256) solve_sweep_kernel(Acc L, T *B, int64_t l
 
 // Workspace bytes for a solve of order n with nrhs right-hand sides.
 inline size_t solve_ws_bytes(int64_t n, int64_t nrhs) {
-    const int64_t nblk = (n + kSB - 1) / kSB, ny = (nrhs + kRC - 1) / kRC;
+    const int rc = solve_rc(nrhs);
+    const int64_t nblk = (n + kSB - 1) / kSB, ny = (nrhs + rc - 1) / rc;
     return sizeof(SolveCtl) + (size_t)2 * nblk * ny * sizeof(int32_t);
 }
 
@@ -368,7 +383,8 @@ inline size_t solve_ws_bytes(int64_t n, int64_t nrhs) {
 template <typename T, class Acc>
 int launch_solve(const Acc &L, T *B, int64_t ldb, int64_t n, int64_t nrhs, void *ws, double timeout_s,
                  cudaStream_t st) {
-    const int64_t nblk = (n + kSB - 1) / kSB, ny = (nrhs + kRC - 1) / kRC;
+    const int rc = solve_rc(nrhs);
+    const int64_t nblk = (n + kSB - 1) / kSB, ny = (nrhs + rc - 1) / rc;
     if (ny > 4096) {
         set_error("argument: nrhs > %d", 4096 * kRC);
         return CHOL_ERR_ARG;
@@ -378,8 +394,13 @@ int launch_solve(const Acc &L, T *B, int64_t ldb, int64_t n, int64_t nrhs, void 
     CHOL_CUDA(cudaMemsetAsync(ws, 0, solve_ws_bytes(n, nrhs), st));
     const uint64_t tns = (uint64_t)(timeout_s * 1e9);
     const dim3 grid((unsigned)nblk, (unsigned)ny);
-    solve_sweep_kernel<T, Acc, true><<<grid, 256, 0, st>>>(L, B, ldb, n, nrhs, flags, ctl, tns);
-    solve_sweep_kernel<T, Acc, false><<<grid, 256, 0, st>>>(L, B, ldb, n, nrhs, flags + nblk * ny, ctl, tns);
+    if (rc == 4) {
+        solve_sweep_kernel<T, Acc, true, 4><<<grid, 256, 0, st>>>(L, B, ldb, n, nrhs, flags, ctl, tns);
+        solve_sweep_kernel<T, Acc, false, 4><<<grid, 256, 0, st>>>(L, B, ldb, n, nrhs, flags + nblk * ny, ctl, tns);
+    } else {
+        solve_sweep_kernel<T, Acc, true, kRC><<<grid, 256, 0, st>>>(L, B, ldb, n, nrhs, flags, ctl, tns);
+        solve_sweep_kernel<T, Acc, false, kRC><<<grid, 256, 0, st>>>(L, B, ldb, n, nrhs, flags + nblk * ny, ctl, tns);
+    }
     CHOL_CUDA(cudaGetLastError());
     return CHOL_OK;
 }

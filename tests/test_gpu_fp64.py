@@ -266,7 +266,8 @@ def test_trace_respects_dependencies():
                 assert ev[nd][1] <= t0, ((ty, I, K, J), nd)
 
 
-def test_solve_exact_integer_factor():
+@pytest.mark.parametrize("nrhs", [3, 5])
+def test_solve_exact_integer_factor(nrhs):
     """L0 with diagonal in {1, 2, 4} and small integer entries, x integer, b = A x:
     every intermediate of both sweeps is an integer, so the solve must return x
     exactly.  The diagonal blocks of L0 are ill-conditioned (kappa_inf about
@@ -278,7 +279,7 @@ def test_solve_exact_integer_factor():
     n = 1000
     A, L0 = si.exact_integer_factor(n, seed=31)
     r = si.rng(32)
-    X0 = r.integers(-3, 4, size=(n, 5)).astype(np.float64)
+    X0 = r.integers(-3, 4, size=(n, nrhs)).astype(np.float64)
     B = A @ X0
     assert np.max(np.abs(B)) < 2.0 ** 50
     dL = chol.colmajor(L0)
