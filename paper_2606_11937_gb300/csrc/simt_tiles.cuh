@@ -61,16 +61,34 @@ __device__ void block_nt_update(T *C, int ldc, const T *A, int lda, const T *B, 
 #pragma unroll
         for (int j = 0; j < MI; ++j) acc[i][j] = T(0);
 
-    for (int k0 = 0; k0 < k; k0 += kBK) {
+    // binary32: the next k-chunk's operands are loaded into registers while the
+    // current one is applied (FFMA leaves the loads' latency exposed); binary64
+    // keeps the register budget that lets two CTAs share an SM (DFMA-bound)
+    constexpr bool kPipe = sizeof(T) == 4;
+    constexpr int NQ = (16 * MI * kBK) / kThreads;
+    T pa[NQ], pb[NQ];
+    auto load_chunk = [&](int k0) {
         const int kc = min(kBK, k - k0);
 #pragma unroll
-        for (int q = 0; q < (16 * MI * kBK) / kThreads; ++q) {
+        for (int q = 0; q < NQ; ++q) {
             const int e = threadIdx.x + kThreads * q;
             const int r = e / kBK, kk = e % kBK;
-            sm.As[kk][r] = (r < m && kk < kc) ? ldg_cg(A + (size_t)r * lda + k0 + kk) : T(0);
-            sm.Bs[kk][r] = (r < n && kk < kc) ? ldg_cg(B + (size_t)r * ldb + k0 + kk) : T(0);
+            pa[q] = (r < m && kk < kc) ? ldg_cg(A + (size_t)r * lda + k0 + kk) : T(0);
+            pb[q] = (r < n && kk < kc) ? ldg_cg(B + (size_t)r * ldb + k0 + kk) : T(0);
+        }
+    };
+    if (kPipe && k > 0) load_chunk(0);
+    for (int k0 = 0; k0 < k; k0 += kBK) {
+        if (!kPipe) load_chunk(k0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int e = threadIdx.x + kThreads * q;
+            const int r = e / kBK, kk = e % kBK;
+            sm.As[kk][r] = pa[q];
+            sm.Bs[kk][r] = pb[q];
         }
         simt_sync();
+        if (kPipe && k0 + kBK < k) load_chunk(k0 + kBK);
 #pragma unroll
         for (int kk = 0; kk < kBK; ++kk) {
             T a[MI], b[MI];
