@@ -231,7 +231,14 @@ int chol_mixed_factor(int64_t n, const double *A, int64_t lda, const chol_opts *
  * backward error (NaN if an iterate was not finite).  Returns
  * CHOL_ERR_NOT_CONVERGED if the tolerance was missed (X then holds the last
  * iterate) and CHOL_ERR_NOT_SPD, without solving, if the handle's
- * factorization broke down (info > 0). */
+ * factorization broke down (info > 0).
+ * For n >= 1024 the residual runs on the tensor cores with binary64 accuracy
+ * (exact bf16 slicing): the first solve on a handle builds the slices of A,
+ * about 16 n^2 bytes of device memory (17 GB at n = 32768), which the handle
+ * keeps until chol_factor_free; when that memory cannot be allocated the
+ * residual runs on the FP64 pipe instead.  With CHOL_FLAG_GMRES_IR (a flag
+ * of the factor call) each refinement step is a GMRES solve preconditioned
+ * with the factor and *iters counts preconditioner applications. */
 int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb,
                      double *X, int64_t ldx, int32_t *iters, double *berr);
 
