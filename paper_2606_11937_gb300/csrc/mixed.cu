@@ -364,9 +364,12 @@ struct MixedBody {
                     ga.mapB[p] = (three && p == 1) ? &g.map_lo : &g.map_hi;
                 }
                 ga.idesc = make_idesc((uint32_t)g.fmt, 128, nb >= 256 ? 256 : 128);
+                // the producer takes the next task from the queues once its
+                // loads are issued, while the tensor cores and the epilogue finish
+                const auto take_ahead = [&a]() { df_take_ahead(a); };
                 const bool ok = tc_tile_update(sm.ts, &sm.stages[0][0], sm.xpose, ga, g.S.tile(I, K), nb,
                                                (int)(ta * nb), (int)(tb * nb), sa, sb, type == T_SYRK, g.timeout_ns,
-                                               Done{g, a}, a.dfl != nullptr, pack_task(m, I, K, J), t0);
+                                               Done{g, a}, a.dfl != nullptr, pack_task(m, I, K, J), t0, take_ahead);
                 if (!ok && threadIdx.x == 0) {
                     if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 3;
                     st_release_s32(&a.ctl->abort, 1);

@@ -314,12 +314,17 @@ __device__ inline bool tc_flush(TcShared &ts, float *xpose, uint64_t timeout_ns,
 // returns false if a wait expired.  A deferred sub-tile of the previous call
 // is applied first by the epilogue warps (its completion handed to on_done);
 // with defer_last (tile of order 128: one sub-tile) this call's epilogue is
-// left for the next call or tc_flush, tagged with task / t0.
-template <class Done = TcNoDone>
+// left for the next call or tc_flush, tagged with task / t0.  The producer
+// thread calls producer_idle() after its last load.
+struct TcNoHook {
+    __device__ void operator()() const {}
+};
+
+template <class Done = TcNoDone, class Hook = TcNoHook>
 __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpose, const TcGemmArgs &g, float *C,
                                       int nb, int aRow0, int bRow0, float sa, float sb, bool lower,
                                       uint64_t timeout_ns, const Done &on_done = Done(), bool defer_last = false,
-                                      uint64_t task = 0, uint64_t t0 = 0) {
+                                      uint64_t task = 0, uint64_t t0 = 0, const Hook &producer_idle = Hook()) {
     const int MH = nb >= 256 ? 2 : 1;          // 128-row halves per sub-tile
     const int NN = nb >= 256 ? 256 : 128;      // MMA N
     const int SR = MH * 128;                   // sub-tile rows
@@ -378,6 +383,7 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
                                         bRow0 + ci * NN + q * 128);
                     }
             }
+        producer_idle();
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer
         uint32_t f = ring0, u = acc0;
