@@ -320,7 +320,7 @@ def run_fp64(args, world, rank, local):
         # chol_factor_host moves, per block of 512 columns from j0, rows j0 .. n-1
         moved = sum((n - j0) * min(512, n - j0) * 8 for j0 in range(0, n, 512))
         e2e = {"value": world * flops / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": moved,
-               "d2h_bytes_per_step": moved}
+               "d2h_bytes_per_step": moved, "seconds_per_call": [round(x, 4) for x in et]}
         del h
 
     cpu = None
