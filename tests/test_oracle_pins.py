@@ -286,3 +286,21 @@ def test_residual_closed_form():
     want = math.sqrt(2 * d * d + d ** 4) / math.sqrt(n)
     assert abs(oracle.residual_fro(np.eye(n), L) - want) < 1e-15
     assert abs(oracle.residual_probe(np.eye(n), L, np.eye(n)) - want) < 1e-15
+
+
+@pytest.mark.parametrize("n,band", [(300, 5), (257, 64)])
+def test_banded_integer_generator_and_oracle(n, band):
+    """The device builder of the full-size exact-integer input (run here on
+    the CPU device) gives A = L0 L0^T exactly (integer arithmetic), L0 banded
+    with diagonal in {1, 2, 4}; the oracle factors A back to L0 exactly."""
+    torch = pytest.importorskip("torch")
+    A, L = si.exact_integer_band_torch(n, band, seed=7, device="cpu")
+    A = A.T.numpy()  # column-major convention: element (i, j) of A
+    L0 = L.T.numpy()  # element (i, j) of L0
+    assert np.array_equal(L0, np.tril(L0))
+    assert np.all(np.isin(np.diag(L0), [1.0, 2.0, 4.0]))
+    assert np.all(np.tril(L0, -band - 1) == 0)
+    Li = L0.astype(np.int64)
+    assert np.array_equal(A.astype(np.int64), Li @ Li.T)
+    Lo, info = oracle.potrf_unblocked(A)
+    assert info == 0 and np.array_equal(np.tril(Lo), L0)
