@@ -86,7 +86,8 @@ typedef enum {
     CHOL_SCHED_TOP_LOOKING = 5      /* the top-looking variant (Section 3.1): block row I in one launch,
                                        one CTA per tile (I, K) applying its updates as the row's tiles
                                        to its left become final, then its TRSM (POTRF for K = I);
-                                       same per-tile update order, same bits */
+                                       same per-tile update order, same bits; its waits for the row's
+                                       tiles are bounded by opts->timeout_s (CHOL_ERR_TIMEOUT) */
 } chol_schedule;
 
 /* opts->flags */
