@@ -97,8 +97,9 @@ enum {
                                     before the other GEMMs (OpenMP 4.5 priorities analog) */
     CHOL_FLAG_GRAPH = 4,         /* launch-ordered schedules: capture the launches into a CUDA graph and
                                     launch it as one unit (the call then waits for it) */
-    CHOL_FLAG_TEST_WITHHOLD = 8, /* dataflow test hook: never release the last POTRF, so the
-                                    bounded waits must expire with CHOL_ERR_TIMEOUT */
+    CHOL_FLAG_TEST_WITHHOLD = 8, /* test hook: never release the last POTRF (dataflow) or tile
+                                    (M-1, 0) (top-looking), so the bounded waits must expire
+                                    with CHOL_ERR_TIMEOUT */
     CHOL_FLAG_FP64_TC = 16,      /* FP64: run SYRK/GEMM on the bf16 tensor cores with binary64
                                     accuracy (exact 8 x 7-bit slicing of row-scaled values, 36
                                     integer-exact products per update); tiles of order 128 */

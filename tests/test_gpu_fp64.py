@@ -230,6 +230,23 @@ def test_withheld_dependency_times_out():
     assert rc == 0 and scaled_error(L, Lref, A) <= TOL_SCALED
 
 
+@pytest.mark.parametrize("flags", [0, 16])
+def test_top_looking_withheld_tile_times_out(flags):
+    """Fault made on the host, top-looking wavefront: tile (M-1, 0) is never
+    published, so the row's other tiles wait until the bounded waits expire:
+    CHOL_ERR_TIMEOUT, and the next factorization on the context is correct
+    (DFMA and tensor-core engines)."""
+    import paper_2606_11937_gb300 as chol
+    A = matrix("gram", 640, 3)
+    nb = 128 if flags else 64
+    _, info, st, rc = gpu_factor(A, schedule="top_looking", nb=nb, flags=flags | chol.CHOL_FLAG_TEST_WITHHOLD,
+                                 timeout_s=0.25)
+    assert rc == chol.CHOL_ERR_TIMEOUT
+    Lref, _ = oracle_factor("gram", 640, 3)
+    L, info, st, rc = gpu_factor(A, schedule="top_looking", nb=nb, flags=flags)
+    assert rc == 0 and scaled_error(L, Lref, A) <= TOL_SCALED
+
+
 def test_trace_respects_dependencies():
     """Per-task %globaltimer records: every task starts after its predecessors
     ended, and each tile's updates run in ascending J."""
