@@ -47,6 +47,12 @@ int chol_test_ozaki_update(const double *A, const double *B, double *C);
 int chol_test_oz_residual(int64_t n, const double *A, int64_t lda, const double *X, int64_t ldx,
                           const double *B, int64_t ldb, double *R, int64_t ldr, int64_t nrhs);
 
+/* Memory the current device has in use, for tests that check that a call
+ * allocates nothing: the device's free bytes (cudaMemGetInfo) and the bytes in
+ * use and reserved by its default stream-ordered pool (the pool the library's
+ * workspaces come from).  Returns CHOL_OK or CHOL_ERR_CUDA. */
+int chol_test_device_memory(uint64_t *free_bytes, uint64_t *pool_used, uint64_t *pool_reserved);
+
 #ifdef __cplusplus
 }
 #endif

@@ -90,6 +90,7 @@ SIGNATURES = {
     "chol_test_tc_update": (ctypes.c_int, [_i32, _i64, _vp, _i32, _i32, _vp, _i32]),
     "chol_test_ozaki_update": (ctypes.c_int, [_vp, _vp, _vp]),
     "chol_test_oz_residual": (ctypes.c_int, [_i64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _i64]),
+    "chol_test_device_memory": (ctypes.c_int, [_P(ctypes.c_uint64), _P(ctypes.c_uint64), _P(ctypes.c_uint64)]),
     "chol_batch_plan": (ctypes.c_int, [_i32, _P(_i64), _P(chol_opts), _P(_vp)]),
     "chol_batch_run": (ctypes.c_int, [_vp, _P(_vp), _P(_i64), _P(_vp), _P(_i64)]),
     "chol_batch_stats": (ctypes.c_int, [_vp, _P(chol_stats)]),

@@ -256,11 +256,22 @@ __device__ __forceinline__ typename Body::Smem &body_smem() {
 template <class Body>
 constexpr size_t body_smem_bytes() { return Body::kSmemBytes + 1024; }
 
+// Whether the launch has been aborted, read once by thread 0 and shared with
+// the CTA (all threads call it; it ends with a barrier), so the whole CTA
+// returns or none of it does: a CTA whose thread 0 left early would never
+// initialise the barriers and tensor memory the other threads then use.
+__device__ __forceinline__ bool fj_cta_aborted(const SchedArgs &a) {
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) s_abort = ld_acquire_s32(&a.ctl->abort);
+    __syncthreads();
+    return s_abort != 0;
+}
+
 template <class Body>
 __global__ void __launch_bounds__(Body::kBlock) fj_potrf_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
                                                        int J) {
     typename Body::Smem &sm = body_smem<Body>();
-    if (ld_acquire_s32(&a.ctl->abort)) return;
+    if (fj_cta_aborted(a)) return;
     Body::cta_init(g, sm);
     Body::run(g, a, 0, J, J, J, sm);
     Body::cta_fini(g, sm);
@@ -270,7 +281,7 @@ template <class Body>
 __global__ void __launch_bounds__(Body::kBlock) fj_trsm_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
                                                       int J) {
     typename Body::Smem &sm = body_smem<Body>();
-    if (ld_acquire_s32(&a.ctl->abort)) return;
+    if (fj_cta_aborted(a)) return;
     Body::cta_init(g, sm);
     Body::run(g, a, 0, J + 1 + (int)blockIdx.x, J, J, sm);
     Body::cta_fini(g, sm);
@@ -281,7 +292,7 @@ template <class Body>
 __global__ void __launch_bounds__(Body::kBlock) fj_update_kernel(const __grid_constant__ typename Body::Args g, SchedArgs a,
                                                         int J) {
     typename Body::Smem &sm = body_smem<Body>();
-    if (ld_acquire_s32(&a.ctl->abort)) return;
+    if (fj_cta_aborted(a)) return;
     int i, k;
     tile_of(blockIdx.x, i, k);
     Body::cta_init(g, sm);
@@ -294,7 +305,7 @@ template <class Body>
 __global__ void __launch_bounds__(Body::kBlock) fj_update_naive_kernel(const __grid_constant__ typename Body::Args g,
                                                               SchedArgs a, int J) {
     typename Body::Smem &sm = body_smem<Body>();
-    if (ld_acquire_s32(&a.ctl->abort)) return;
+    if (fj_cta_aborted(a)) return;
     const int I = J + 1 + (int)blockIdx.x;
     Body::cta_init(g, sm);
     for (int K = J + 1; K <= I; ++K) Body::run(g, a, 0, I, K, J, sm);
@@ -307,7 +318,7 @@ template <class Body>
 __global__ void __launch_bounds__(Body::kBlock) fj_left_update_kernel(const __grid_constant__ typename Body::Args g,
                                                              SchedArgs a, int K) {
     typename Body::Smem &sm = body_smem<Body>();
-    if (ld_acquire_s32(&a.ctl->abort)) return;
+    if (fj_cta_aborted(a)) return;
     const int I = K + (int)blockIdx.x;
     Body::cta_init(g, sm);
     for (int J = 0; J < K; ++J) Body::run(g, a, 0, I, K, J, sm);
@@ -330,11 +341,11 @@ __global__ void __launch_bounds__(Body::kBlock) fj_top_row_kernel(const __grid_c
     __shared__ int s_k, s_ok;
     if (threadIdx.x == 0) {
         s_k = (int)(atomicAdd(&a.ctl->ticket, 1ull) - (unsigned long long)I * (I + 1) / 2);
-        s_ok = 1;
+        s_ok = ld_acquire_s32(&a.ctl->abort) ? 0 : 1;
     }
     __syncthreads();
     const int K = s_k;
-    if (ld_acquire_s32(&a.ctl->abort)) return;
+    if (!s_ok) return;  // the whole CTA, on the one value thread 0 read
     Body::cta_init(g, sm);
     const uint64_t deadline = global_ns() + timeout_ns;
     for (int J = 0; J < K; ++J) {

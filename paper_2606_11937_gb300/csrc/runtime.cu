@@ -79,3 +79,20 @@ const char *chol_last_error(void) { return chol::g_err; }
 const char *chol_version(void) { return "gb300-cholesky 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+extern "C" int chol_test_device_memory(uint64_t *free_bytes, uint64_t *pool_used, uint64_t *pool_reserved) {
+    CHOL_CHECK_ARG(free_bytes && pool_used && pool_reserved, "NULL pointer");
+    int dev = 0;
+    CHOL_CUDA(cudaGetDevice(&dev));
+    size_t fr = 0, tot = 0;
+    CHOL_CUDA(cudaMemGetInfo(&fr, &tot));
+    cudaMemPool_t pool;
+    CHOL_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t used = 0, res = 0;
+    CHOL_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    CHOL_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &res));
+    *free_bytes = fr;
+    *pool_used = used;
+    *pool_reserved = res;
+    return CHOL_OK;
+}

@@ -110,12 +110,18 @@ int chol_solve_noalloc(int64_t n, int64_t nrhs, const double *L, int64_t ldl, do
         scratch = g_noalloc_addr[dev];
     }
     cudaStream_t st = (cudaStream_t)stream;
+    cudaGetLastError();  // errors left by earlier, unrelated runtime calls are not ours to report
     // launch_solve clears the control block and flags it uses before the sweeps
     int rc = launch_solve<double, ColMajorL<double>>(ColMajorL<double>{L, ldl}, B, ldb, n, nrhs, scratch, 60.0, st);
-    if (rc != CHOL_OK) return rc;
     int32_t h[2] = {0, 0};
-    CHOL_CUDA(cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
-    CHOL_CUDA(cudaStreamSynchronize(st));
+    if (rc == CHOL_OK && cudaMemcpyAsync(h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "solve readback", __FILE__, __LINE__);
+    // whatever happened, return only once the work queued on the stream has
+    // finished: a caller that retries after an error must not overlap kernels
+    // of this call that still write B and the shared scratch
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (rc != CHOL_OK) return rc;
+    if (es != cudaSuccess) return cuda_fail(es, "solve sync", __FILE__, __LINE__);
     if (h[0]) {
         set_error("solve: device-side wait expired (site %d)", h[1]);
         return h[0];

@@ -1,6 +1,7 @@
-"""Parity at the benchmark's full size (n = 32768), in the launch configuration
-bench.py times (FP64 on the tensor cores, dataflow schedule with priorities,
-tiles of order 128), through properties that hold at any size:
+"""Parity at the benchmark's full sizes (n = 32768 and n = 65536, the order
+bench.py times by default), in the launch configuration bench.py times (FP64
+on the tensor cores, dataflow schedule with priorities, tiles of order 128),
+through properties that hold at any size:
 
 * exact-integer pin: A = L0 L0^T with a banded integer L0 (diagonal in
   {1, 2, 4}, entries in {-2 .. 2}): every intermediate is a small integer, so
@@ -8,6 +9,10 @@ tiles of order 128), through properties that hold at any size:
 * the bench's own input (SE covariance, nugget 1e-2, seed 1): randomized
   residual ||A X - L (L^T X)||_F / ||A X||_F <= 1e-14 sqrt(n) with Gaussian
   probes (the products in binary64 on the device);
+* the host-buffer entry point at n = 65536 (the first order whose n^2
+  elements exceed 2^31, so every 64-bit element offset of the copies, the
+  repack and the unpack is exercised): the exact-integer factor comes back
+  into pinned host memory bit for bit;
 * the mixed-precision configuration (FP32 factor, 16 right-hand sides,
   refinement to 1e-14): the normwise backward error recomputed from A, X and
   B independently of the library's own estimate.
@@ -21,50 +26,82 @@ import seeded_inputs as si
 pytestmark = pytest.mark.gpu
 
 N = 32768
+SIZES = (32768, 65536)
+BLK = 4096  # column block of the comparisons (bounded temporaries)
+
+
+def _bench_opts():
+    import paper_2606_11937_gb300 as chol
+    return chol.opts(schedule="dataflow", nb=128, flags=chol.CHOL_FLAG_FP64_TC | chol.CHOL_FLAG_PRIORITY)
 
 
 def _factor_tc(dA):
     import torch
 
     import paper_2606_11937_gb300 as chol
-    rc, info, st = chol.chol_factor_ex(
-        dA, chol.opts(schedule="dataflow", nb=128, flags=chol.CHOL_FLAG_FP64_TC | chol.CHOL_FLAG_PRIORITY),
-        raise_on_error=False)
+    rc, info, st = chol.chol_factor_ex(dA, _bench_opts(), raise_on_error=False)
     torch.cuda.synchronize()
     return rc, info, st
 
 
-def test_fullsize_exact_integer_factor():
+def _assert_lower_equal(got, want, n):
+    """Lower triangles of two column-major (n, n) tensors equal bit for bit;
+    `got` may live in host memory (its blocks are copied to the device)."""
     import torch
-    A, L = si.exact_integer_band_torch(N, band=64, seed=41)
+    for c0 in range(0, n, BLK):
+        c1 = min(n, c0 + BLK)
+        g = got[:, c0:c1].to("cuda")
+        assert torch.equal(torch.tril(g, diagonal=-c0), torch.tril(want[:, c0:c1], diagonal=-c0)), c0
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_fullsize_exact_integer_factor(n):
+    A, L = si.exact_integer_band_torch(n, band=64, seed=41)
     dA = A.T  # column-major view of the symmetric A
     rc, info, st = _factor_tc(dA)
     assert rc == 0 and info == 0
-    want = L.T  # element (i, j) of the column-major L0
-    del A
-    # compare the lower triangles in column blocks (bounded temporaries)
-    for c0 in range(0, N, 4096):
-        c1 = c0 + 4096
-        got = torch.tril(dA[:, c0:c1], diagonal=-c0)
-        ref = torch.tril(want[:, c0:c1], diagonal=-c0)
-        assert torch.equal(got, ref), c0
+    _assert_lower_equal(dA, L.T, n)  # L.T: element (i, j) of the column-major L0
 
 
-def test_fullsize_bench_input_residual():
+@pytest.mark.parametrize("n", SIZES)
+def test_fullsize_bench_input_residual(n):
     import torch
-    A = si.se_covariance_torch(N, seed=1, lengthscale=0.1, nugget=1e-2).T
+    A = si.se_covariance_torch(n, seed=1, lengthscale=0.1, nugget=1e-2).T  # symmetric: both triangles
     L = A.clone()
     rc, info, st = _factor_tc(L)
     assert rc == 0 and info == 0
-    L = torch.tril(L)
     g = torch.Generator(device="cuda")
     g.manual_seed(99)
-    X = torch.randn((N, 4), dtype=torch.float64, device="cuda", generator=g)
-    AX = torch.tril(A) @ X + torch.tril(A, -1).T @ X  # A from its lower triangle
-    R = AX - L @ (L.T @ X)
-    rel = float(torch.linalg.norm(R) / torch.linalg.norm(AX))
-    print(f"n={N}: probe residual {rel:.3e} (bound {1e-14 * math.sqrt(N):.3e})")
-    assert rel <= 1e-14 * math.sqrt(N)
+    X = torch.randn((n, 4), dtype=torch.float64, device="cuda", generator=g)
+    AX = A @ X
+    del A
+    # Y = L^T X and L Y by column blocks of the lower triangle of L
+    Y = torch.empty_like(X)
+    for c0 in range(0, n, BLK):
+        c1 = min(n, c0 + BLK)
+        Y[c0:c1] = torch.tril(L[:, c0:c1], diagonal=-c0).T @ X
+    LY = torch.zeros_like(X)
+    for c0 in range(0, n, BLK):
+        c1 = min(n, c0 + BLK)
+        LY += torch.tril(L[:, c0:c1], diagonal=-c0) @ Y[c0:c1]
+    rel = float(torch.linalg.norm(AX - LY) / torch.linalg.norm(AX))
+    print(f"n={n}: probe residual {rel:.3e} (bound {1e-14 * math.sqrt(n):.3e})")
+    assert rel <= 1e-14 * math.sqrt(n)
+
+
+def test_fullsize_host_buffer_roundtrip_65536():
+    import torch
+
+    import paper_2606_11937_gb300 as chol
+    n = 65536
+    A, L = si.exact_integer_band_torch(n, band=32, seed=43)
+    h = torch.empty_strided((n, n), (1, n), dtype=torch.float64, pin_memory=True)
+    h.copy_(A.T)
+    del A
+    torch.cuda.synchronize()
+    info, st = chol.chol_factor_host(h, _bench_opts())
+    assert info == 0
+    _assert_lower_equal(h, L.T, n)
 
 
 def test_fullsize_mixed_refinement_backward_error():
