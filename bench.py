@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--workload", default="fp64", choices=["fp64", "mixed", "batched", "serve", "sweep"])
     p.add_argument("--sweep-nb", default="")
     p.add_argument("--sweep-sched", default="")
+    p.add_argument("--sweep-engine", default="", help="sweep: tc (tensor-core FP64 engine), simt (DFMA engine)")
     p.add_argument("--noop", action="store_true")
     p.add_argument("--trace", action="store_true")
     p.add_argument("--batch-count", type=int, default=4096)

@@ -184,46 +184,51 @@ def run_sweep(args, world, rank, local):
     A0 = si.se_covariance_torch(n, seed=1, lengthscale=0.1, nugget=1e-2, device=dev).T
     A = torch.empty_strided((n, n), (1, n), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    nbs = [int(x) for x in (args.sweep_nb or "64,128,256,512").split(",")]
+    nbs = [int(x) for x in (args.sweep_nb or "128,256,512,1024").split(",")]
     scheds = (args.sweep_sched or "dataflow,fork_join,fork_join_naive").split(",")
+    engines = (args.sweep_engine or "tc").split(",")
     import ctypes
     import numpy as np
     rsz = ctypes.sizeof(chol.chol_trace_rec)
-    for nb in nbs:
-        for sched in scheds:
-            for flags in ([0, chol.CHOL_FLAG_NOOP] if args.noop else [0]):
-                fl = flags | (args.flags & ~chol.CHOL_FLAG_NOOP)
-                m = -(-n // nb)
-                ntask = m * (m + 1) * (m + 2) // 6
-                trace = torch.empty(ntask * rsz, dtype=torch.uint8, device=dev) if args.trace else None
-                o = chol.opts(schedule=sched, nb=nb, flags=fl, stream=stream.cuda_stream, num_ctas=args.num_ctas,
-                              trace=trace, trace_capacity=ntask if args.trace else 0)
-                ts = []
-                for _ in range(max(1, args.steps)):
-                    A.copy_(A0)
-                    torch.cuda.synchronize()
-                    rc, info, st = chol.chol_factor_ex(A, o)
-                    ts.append(st.device_ms)
-                ms = statistics.median(ts)
-                tasks = sum(st.tasks)
-                rec = {"workload": "sweep", "n": n, "nb": nb, "schedule": sched, "noop": bool(flags),
-                       "flags": fl, "ms": ms, "tflops": (n ** 3 / 3) / (ms / 1e3) / 1e12 if not flags else None,
-                       "tasks": tasks, "us_per_task": 1e3 * ms / tasks, "launches": st.launches}
-                if trace is not None:
-                    raw = trace.cpu().numpy()[: min(st.trace_records, ntask) * rsz]
-                    r = raw.view(np.dtype([("type", "<i4"), ("I", "<i4"), ("K", "<i4"), ("J", "<i4"),
-                                           ("sm", "<i4"), ("matrix", "<i4"), ("t0", "<u8"), ("t1", "<u8")]))
-                    busy_ns = float(np.sum(r["t1"] - r["t0"]))
-                    ctas = args.num_ctas or 152 * (1 if fl & chol.CHOL_FLAG_FP64_TC else 4)
-                    span_ns = float(r["t1"].max() - r["t0"].min())
-                    dur = (r["t1"] - r["t0"]).astype(np.float64)
-                    by_type = {name: float(np.mean(dur[r["type"] == ty]) / 1e3) if np.any(r["type"] == ty) else None
-                               for ty, name in enumerate(("potrf", "trsm", "syrk", "gemm"))}
-                    rec.update({"trace_busy_s": busy_ns / 1e9, "trace_span_s": span_ns / 1e9, "ctas": ctas,
-                                "idle_us_per_task": (ctas * span_ns - busy_ns) / 1e3 / len(r),
-                                "mean_task_us": busy_ns / 1e3 / len(r), "mean_us_by_type": by_type})
-                if rank == 0:
-                    print(json.dumps(rec), flush=True)
+    eflags = {"tc": chol.CHOL_FLAG_FP64_TC | chol.CHOL_FLAG_PRIORITY, "simt": chol.CHOL_FLAG_FP64_SIMT}
+    points = [(e, nb, sched) for e in engines for nb in nbs for sched in scheds
+              if not (e == "tc" and nb % 128)]
+    for engine, nb, sched in points:
+        for flags in ([0, chol.CHOL_FLAG_NOOP] if args.noop else [0]):
+            fl = flags | eflags[engine] | (args.flags & ~chol.CHOL_FLAG_NOOP)
+            if sched != "dataflow":
+                fl &= ~chol.CHOL_FLAG_PRIORITY
+            m = -(-n // nb)
+            ntask = m * (m + 1) * (m + 2) // 6
+            trace = torch.empty(ntask * rsz, dtype=torch.uint8, device=dev) if args.trace else None
+            o = chol.opts(schedule=sched, nb=nb, flags=fl, stream=stream.cuda_stream, num_ctas=args.num_ctas,
+                          trace=trace, trace_capacity=ntask if args.trace else 0)
+            ts = []
+            for _ in range(max(1, args.steps)):
+                A.copy_(A0)
+                torch.cuda.synchronize()
+                rc, info, st = chol.chol_factor_ex(A, o)
+                ts.append(st.device_ms)
+            ms = statistics.median(ts)
+            tasks = sum(st.tasks)
+            rec = {"workload": "sweep", "engine": engine, "n": n, "nb": nb, "schedule": sched, "noop": bool(flags),
+                   "flags": fl, "ms": ms, "tflops": (n ** 3 / 3) / (ms / 1e3) / 1e12 if not flags else None,
+                   "tasks": tasks, "us_per_task": 1e3 * ms / tasks, "launches": st.launches}
+            if trace is not None:
+                raw = trace.cpu().numpy()[: min(st.trace_records, ntask) * rsz]
+                r = raw.view(np.dtype([("type", "<i4"), ("I", "<i4"), ("K", "<i4"), ("J", "<i4"),
+                                       ("sm", "<i4"), ("matrix", "<i4"), ("t0", "<u8"), ("t1", "<u8")]))
+                busy_ns = float(np.sum(r["t1"] - r["t0"]))
+                ctas = args.num_ctas or 152 * (1 if fl & chol.CHOL_FLAG_FP64_TC else 4)
+                span_ns = float(r["t1"].max() - r["t0"].min())
+                dur = (r["t1"] - r["t0"]).astype(np.float64)
+                by_type = {name: float(np.mean(dur[r["type"] == ty]) / 1e3) if np.any(r["type"] == ty) else None
+                           for ty, name in enumerate(("potrf", "trsm", "syrk", "gemm"))}
+                rec.update({"trace_busy_s": busy_ns / 1e9, "trace_span_s": span_ns / 1e9, "ctas": ctas,
+                            "idle_us_per_task": (ctas * span_ns - busy_ns) / 1e3 / len(r),
+                            "mean_task_us": busy_ns / 1e3 / len(r), "mean_us_by_type": by_type})
+            if rank == 0:
+                print(json.dumps(rec), flush=True)
 
 
 def run(args, world, rank, local):

@@ -100,9 +100,18 @@ enum {
     CHOL_FLAG_TEST_WITHHOLD = 8, /* test hook: never release the last POTRF (dataflow) or tile
                                     (M-1, 0) (top-looking), so the bounded waits must expire
                                     with CHOL_ERR_TIMEOUT */
-    CHOL_FLAG_FP64_TC = 16,      /* FP64: run SYRK/GEMM on the bf16 tensor cores with binary64
-                                    accuracy (exact 8 x 7-bit slicing of row-scaled values, 36
-                                    integer-exact products per update); tiles of order 128 */
+    CHOL_FLAG_FP64_TC = 16,      /* FP64: run SYRK/GEMM (and TRSM, as a product with the inverted
+                                    diagonal block when it is well conditioned) on the bf16 tensor
+                                    cores with binary64 accuracy (exact 8 x 7-bit slicing of
+                                    row-scaled values, 36 integer-exact products per 128 x 128
+                                    block update); tile orders 128 r (r = 1 .. 16), each task
+                                    running its r x r blocks of order 128 in the order the
+                                    algorithm gives them at tile order 128, so every tile order
+                                    gives the same bits.  This is the DEFAULT engine for n > 1024
+                                    when nb is 0 (then 128) or a multiple of 128 up to 2048 */
+    CHOL_FLAG_FP64_SIMT = 64,    /* FP64: run every tile kernel on the CUDA cores in binary64 (DFMA),
+                                    the default for n <= 1024 or tile orders that are not multiples
+                                    of 128 */
     CHOL_FLAG_GMRES_IR = 32      /* chol_mixed_solve: each refinement step solves the correction
                                     equation by GMRES(20) preconditioned with the low-precision
                                     factor (binary64 Krylov vectors) instead of one solve with it;

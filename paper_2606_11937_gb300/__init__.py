@@ -27,6 +27,7 @@ CHOL_SCHED_AUTO, CHOL_SCHED_FORK_JOIN, CHOL_SCHED_FORK_JOIN_NAIVE, CHOL_SCHED_DA
 CHOL_SCHED_LEFT_LOOKING, CHOL_SCHED_TOP_LOOKING = 4, 5
 CHOL_FLAG_NOOP, CHOL_FLAG_PRIORITY, CHOL_FLAG_GRAPH, CHOL_FLAG_TEST_WITHHOLD, CHOL_FLAG_FP64_TC = 1, 2, 4, 8, 16
 CHOL_FLAG_GMRES_IR = 32
+CHOL_FLAG_FP64_SIMT = 64
 
 PRECISIONS = {"fp64": CHOL_FP64, "fp32": CHOL_FP32, "tf32": CHOL_TF32, "bf16": CHOL_BF16, "fp16": CHOL_FP16}
 SCHEDULES = {"auto": CHOL_SCHED_AUTO, "fork_join": CHOL_SCHED_FORK_JOIN,

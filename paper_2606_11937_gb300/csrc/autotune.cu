@@ -139,7 +139,9 @@ int chol_autotune(int64_t n, int32_t precision, const char *cache_path, double b
     }
     std::vector<int64_t> nbs;
     if (precision == CHOL_FP64) {
-        for (int64_t c : {32, 64, 128, 256, 512})
+        // 32 and 64 run on the DFMA engine; multiples of 128 above order 1024
+        // on the tensor-core engine (the default engine is a function of n, nb)
+        for (int64_t c : {32, 64, 128, 256, 512, 1024})
             if (c <= n || nbs.empty()) nbs.push_back(c);
     } else {
         for (int64_t c : {128, 256, 512})

@@ -35,6 +35,13 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 chol_opts resolve_opts(const chol_opts *opts);
 int num_sms();
 
+// FP64 engine choice (factor.cu): the tensor-core engine by default above
+// order kFp64TcMinN for tile orders that are multiples of 128 up to
+// kFp64TcMaxNb; CHOL_FLAG_FP64_TC / CHOL_FLAG_FP64_SIMT force one engine.
+constexpr int64_t kFp64TcMinN = 1024;
+constexpr int64_t kFp64TcMaxNb = 2048;
+bool fp64_uses_tc(int64_t n, int64_t nb, int32_t flags);
+
 // ----------------------------------------------------------------- tile store
 // Lower tiles (I, K), K <= I, of order nb, each stored contiguously and
 // ROW-major inside (element (r, c) at r * nb + c); tile (I, K) has index

@@ -19,8 +19,19 @@ namespace chol {
 
 template struct TileStore<double>;
 
-int fp64tc_schedule(double *store, int64_t n, Control *ctl, unsigned long long *queue, int32_t *deps, int sched,
-                    const chol_opts &o, cudaStream_t st, int *launches, cudaEvent_t e0);
+int fp64tc_schedule(double *store, int64_t n, int64_t nb, Control *ctl, unsigned long long *queue, int32_t *deps,
+                    int sched, const chol_opts &o, cudaStream_t st, int *launches, cudaEvent_t e0);
+
+// The FP64 engine a call runs, a pure function of (n, nb, flags): the
+// tensor-core engine (SYRK/GEMM/TRSM as exact bf16 slice products) when asked
+// for, or by default above order 1024 (where it is faster: measured equal at
+// n = 1024, 1.5x at 1536, 4x at 6144) for tile orders that are multiples of
+// 128; otherwise the DFMA engine.
+bool fp64_uses_tc(int64_t n, int64_t nb, int32_t flags) {
+    if (flags & CHOL_FLAG_FP64_SIMT) return false;
+    if (flags & CHOL_FLAG_FP64_TC) return true;
+    return n > kFp64TcMinN && (nb == 0 || (nb % 128 == 0 && nb <= kFp64TcMaxNb));
+}
 
 // Allocation layout of one FP64 factorization.
 struct FactorWs {
@@ -33,15 +44,18 @@ struct FactorWs {
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Repack A into `store` (tile order nb), run the schedule, optionally unpack
-// the factor into A_out, read back the control block and synchronize.
+// Repack A into `store` (tile order nb; the tensor-core engine stores tiles
+// of order 128 and runs tasks on tiles of order tc_nb), run the schedule,
+// optionally unpack the factor into A_out, read back the control block and
+// synchronize.
 static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o, double *store, int64_t nb,
-                     int64_t *info, chol_stats *stats, double *A_out, int64_t lda_out) {
+                     int64_t tc_nb, int64_t *info, chol_stats *stats, double *A_out, int64_t lda_out) {
     const int64_t M = (n + nb - 1) / nb;
     const int sched = o.schedule == CHOL_SCHED_AUTO ? CHOL_SCHED_DATAFLOW : o.schedule;
     CHOL_CHECK_ARG(sched >= CHOL_SCHED_FORK_JOIN && sched <= CHOL_SCHED_TOP_LOOKING, "unknown schedule");
     cudaStream_t st = (cudaStream_t)o.stream;
-    const int64_t ntasks = num_tasks(M);
+    const int64_t Mt = tc_nb ? (n + tc_nb - 1) / tc_nb : M;  // tiles per dimension of the tasks
+    const int64_t ntasks = num_tasks(Mt);
     const size_t ctl_bytes = align256(sizeof(Control));
     const size_t q_bytes = sched == CHOL_SCHED_DATAFLOW ? align256((size_t)2 * ntasks * 8) : 0;
     const size_t d_bytes = sched == CHOL_SCHED_DATAFLOW ? align256((size_t)ntasks * 4) : 0;
@@ -63,8 +77,8 @@ static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "event", __FILE__, __LINE__); break; }
         TileStore<double> S{ws.store, (int32_t)nb, (int32_t)M};
         SchedArgs a{ws.ctl, o.trace, o.trace_capacity, o.flags, 0};
-        if (o.flags & CHOL_FLAG_FP64_TC) {
-            rc = fp64tc_schedule(ws.store, n, ws.ctl, ws.queue, ws.deps, sched, o, st, &launches, e0);
+        if (tc_nb) {
+            rc = fp64tc_schedule(ws.store, n, tc_nb, ws.ctl, ws.queue, ws.deps, sched, o, st, &launches, e0);
         } else if (sched == CHOL_SCHED_DATAFLOW) {
             rc = run_dataflow<double>(S, a, ws.queue, ws.deps, o, st, &launches, e0);
         } else {
@@ -83,7 +97,7 @@ static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o
         *info = h.info;
         if (stats) {
             for (int i = 0; i < 4; ++i) stats->tasks[i] = (int64_t)h.tasks[i];
-            stats->nb = nb;
+            stats->nb = tc_nb ? tc_nb : nb;
             stats->schedule = sched;
             stats->launches = launches + (A_out ? 2 : 1);
             stats->trace_records = (int64_t)h.trace_count;
@@ -99,9 +113,11 @@ static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o
     return rc;
 }
 
-static int64_t resolve_nb(int64_t n, const chol_opts &o) {
-    if (o.flags & CHOL_FLAG_FP64_TC) return 128;  // the tensor-core FP64 body works on 128 x 128 tiles
-    return o.nb > 0 ? o.nb : chol_default_nb(n, CHOL_FP64);
+// Tile order of the tasks: the caller's nb, else the default (128 on the
+// tensor-core engine, chol_default_nb on the DFMA engine).
+static int64_t task_nb(int64_t n, const chol_opts &o, bool tc) {
+    if (o.nb > 0) return o.nb;
+    return tc ? 128 : chol_default_nb(n, CHOL_FP64);
 }
 
 size_t fp64_store_bytes(int64_t n, int64_t nb) {
@@ -109,34 +125,45 @@ size_t fp64_store_bytes(int64_t n, int64_t nb) {
     return align256((size_t)num_tiles(M) * nb * nb * sizeof(double));
 }
 
+static int check_tc_nb(int64_t nb) {
+    CHOL_CHECK_ARG(nb % 128 == 0 && nb >= 128 && nb <= kFp64TcMaxNb,
+                   "the tensor-core FP64 engine takes tile orders that are multiples of 128, up to 2048");
+    return CHOL_OK;
+}
+
 static int factor_fp64_device(int64_t n, double *A, int64_t lda, const chol_opts &o, int64_t *info,
                               chol_stats *stats) {
-    const int64_t nb = resolve_nb(n, o);
-    CHOL_CHECK_ARG(nb >= 1 && nb <= 2048, "nb must be in [1, 2048]");
-    CHOL_CHECK_ARG(!(o.flags & CHOL_FLAG_FP64_TC) || o.nb == 0 || o.nb == 128,
-                   "CHOL_FLAG_FP64_TC works on tiles of order 128 (nb = 0 or 128)");
+    const bool tc = fp64_uses_tc(n, o.nb, o.flags);
+    const int64_t tnb = task_nb(n, o, tc);
+    CHOL_CHECK_ARG(tnb >= 1 && tnb <= 2048, "nb must be in [1, 2048]");
+    if (tc && check_tc_nb(tnb) != CHOL_OK) return CHOL_ERR_ARG;
+    const int64_t nb = tc ? 128 : tnb;  // tile order of the store
     CHOL_CHECK_ARG((n + nb - 1) / nb < 65536, "too many tiles per dimension (n / nb must be < 65536)");
     cudaStream_t st = (cudaStream_t)o.stream;
     prepare_pool();
     double *store = nullptr;
     CHOL_CUDA(cudaMallocAsync((void **)&store, fp64_store_bytes(n, nb), st));
-    const int rc = fp64_core(n, A, lda, o, store, nb, info, stats, A, lda);
+    const int rc = fp64_core(n, A, lda, o, store, nb, tc ? tnb : 0, info, stats, A, lda);
     cudaFreeAsync(store, st);
     return rc;
 }
 
 // Factor into a tile store that the caller keeps (freed with cudaFreeAsync);
-// used by the server for resident factors.
+// used by the server for resident factors.  *nb_out is the store's tile
+// order (128 on the tensor-core engine).
 int fp64_factor_store(int64_t n, const double *A, int64_t lda, const chol_opts &o, double **store_out,
                       int64_t *nb_out, int64_t *info) {
     *store_out = nullptr;
-    const int64_t nb = resolve_nb(n, o);
+    const bool tc = fp64_uses_tc(n, o.nb, o.flags);
+    const int64_t tnb = task_nb(n, o, tc);
+    if (tc && check_tc_nb(tnb) != CHOL_OK) return CHOL_ERR_ARG;
+    const int64_t nb = tc ? 128 : tnb;
     CHOL_CHECK_ARG(nb >= 1 && nb <= 2048 && (n + nb - 1) / nb < 65536, "bad tile order");
     cudaStream_t st = (cudaStream_t)o.stream;
     prepare_pool();
     double *store = nullptr;
     CHOL_CUDA(cudaMallocAsync((void **)&store, fp64_store_bytes(n, nb), st));
-    const int rc = fp64_core(n, A, lda, o, store, nb, info, nullptr, nullptr, 0);
+    const int rc = fp64_core(n, A, lda, o, store, nb, tc ? tnb : 0, info, nullptr, nullptr, 0);
     if (rc != CHOL_OK) {
         cudaFreeAsync(store, st);
         return rc;

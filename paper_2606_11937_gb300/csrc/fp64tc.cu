@@ -35,6 +35,8 @@ struct OzArgs {
     double *wbuf;           // per block column J: L_JJ^{-T} in binary64 (row-major)
     int32_t *wflag;         // per block column J: 1 if its TRSMs use W_J (kappa_inf(L_JJ) <= kTrsmKappa)
     uint64_t timeout_ns;
+    int32_t r;              // the task's tile order is 128 r (r x r subtiles of order 128)
+    int32_t Ml;             // tiles of order 128 r per dimension (S.M counts the subtiles)
 };
 
 // The FP64 diagonal factorization in shared memory (potrf128.cuh) over the B
@@ -166,6 +168,17 @@ __device__ double oz_trtri128(OzSmem &sm, double *Wout) {
 // with it); a worse-conditioned diagonal tile keeps the substitution TRSM.
 constexpr double kTrsmKappa = 65536.0;
 
+// Word of a deferred quarter that completes no task: an update inside a
+// multi-update task (tile order 128 r, r > 1) whose last quarter the next
+// update of the same task applies.
+constexpr uint64_t kOzNoTask = ~0ull;
+
+// Task bodies on tiles of order nb = 128 r.  The tile store, the slices and
+// the inverted diagonal blocks stay on 128 x 128 blocks ("subtiles"); a task
+// on a tile of order 128 r runs the operations of its subtiles in the order
+// the tiled algorithm gives them at tile order 128 (every subtile receives
+// its updates in ascending subtile column), so every tile order gives the
+// same bits.  Subtiles past the matrix's last 128-block are skipped.
 struct OzBody {
     using Args = OzArgs;
     using Smem = OzSmem;
@@ -182,101 +195,175 @@ struct OzBody {
     static __device__ __forceinline__ bool absorbs(const Args &g, int I, int K, int J) {
         const int type = task_type(I, K, J);
         if (type == T_POTRF) return false;
-        if (type == T_TRSM) return __ldcg(g.wflag + J) != 0;  // the emulated TRSM is a tile update
+        if (type == T_TRSM) return g.r == 1 && __ldcg(g.wflag + J) != 0;  // the emulated TRSM is a tile update
         return true;
+    }
+    static __device__ void fail_timeout(const SchedArgs &a) {
+        if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 4;
+        st_release_s32(&a.ctl->abort, 1);
     }
     static __device__ void flush(const Args &g, const SchedArgs &a, Smem &sm) {
         const bool ok = ozaki_flush(sm, g.timeout_ns, Done{g, a});
-        if (!ok && threadIdx.x == 0) {
-            if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 4;
-            st_release_s32(&a.ctl->abort, 1);
-        }
+        if (!ok && threadIdx.x == 0) fail_timeout(a);
+    }
+    // apply a deferred quarter inside a task (all threads); false if a wait expired
+    static __device__ bool flush_sub(const Args &g, const SchedArgs &a, Smem &sm) {
+        return ozaki_flush(sm, g.timeout_ns, Done{g, a});
     }
     // completion of a deferred update (one epilogue thread)
     struct Done {
         const Args &g;
         const SchedArgs &a;
         __device__ void operator()(uint64_t w, uint64_t t0) const {
+            if (w == kOzNoTask) return;
             df_complete_lagged<OzBody>(g, a, (int)(w >> 48), (int)((w >> 32) & 0xffff), (int)((w >> 16) & 0xffff),
                                        (int)(w & 0xffff), t0);
         }
     };
     static __device__ __forceinline__ void cta_init(const Args &, Smem &sm) { oz_cta_init(sm.os); }
     static __device__ __forceinline__ void cta_fini(const Args &, Smem &sm) { oz_cta_fini(sm.os); }
-    static __device__ __forceinline__ int tiles(const Args &g, int) { return g.S.M; }
+    static __device__ __forceinline__ int tiles(const Args &g, int) { return g.Ml; }
     static __device__ __forceinline__ int64_t task_base(const Args &, int) { return 0; }
+
+    // POTRF of diagonal subtile j, then (unless it is the last) the inverse
+    // W_j = L_jj^{-1} from the factor still in shared memory and, when it is
+    // well conditioned, its slices.  False (uniform) if a pivot failed; the
+    // failing column is reported.
+    static __device__ bool potrf_sub(const Args &g, const SchedArgs &a, int j, Smem &sm) {
+        const TileStore<double> &S = g.S;
+        const int li = oz_potrf128(S.tile(j, j), sm);
+        if (li) {
+            if (threadIdx.x == 0) {
+                report_info(a.ctl, (int64_t)j * kOzNb + li);
+                st_release_s32(&a.ctl->abort, 1);
+            }
+            return false;
+        }
+        if (j < S.M - 1) {
+            double *W = g.wbuf + (size_t)j * kOzNb * kOzNb;
+            const double kappa = oz_trtri128(sm, W);
+            const bool use_w = kappa <= kTrsmKappa;  // false also for a NaN
+            if (use_w) ozaki_split(W, g.wslices + (size_t)j * kOzS * kOzNb * kOzNb, g.wexp + (size_t)j * kOzNb);
+            if (threadIdx.x == 0) g.wflag[j] = use_w ? 1 : 0;
+            __syncthreads();
+        }
+        return true;
+    }
+    // TRSM of subtile (i, j): substitution on the CUDA cores, or the emulated
+    // product with W_j on the tensor cores; then the solution's slices.
+    // False if a wait expired.
+    template <class Hook>
+    static __device__ bool trsm_sub(const Args &g, const SchedArgs &a, int i, int j, Smem &sm, const Hook &hook) {
+        const TileStore<double> &S = g.S;
+        const int64_t t = tile_index(i, j);
+        double *X = S.tile(i, j);
+        __nv_bfloat16 *sl = g.slices + (size_t)t * kOzS * kOzNb * kOzNb;
+        if (!__ldcg(g.wflag + j)) {  // substitution on the CUDA cores (threads 0..255)
+            SimtSmem<double> &ss = *reinterpret_cast<SimtSmem<double> *>(sm.B);
+            if (threadIdx.x < kThreads) tile_trsm(X, S.tile(j, j), kOzNb, ss);
+            __syncthreads();
+            ozaki_split(X, sl, g.rexp + t * kOzNb);
+            return true;
+        }
+        // A_ij L_jj^{-T} = A_ij W_j^T on the tensor cores: the slices of -A_ij
+        // go to this subtile's slice slot, the subtile is cleared, the emulated
+        // update C -= (-A_ij) W_j^T leaves the solution in it, and the
+        // solution's own slices replace those of -A_ij.
+        ozaki_split(X, sl, g.rexp + t * kOzNb, true, false);
+        for (int e = threadIdx.x; e < kOzNb * kOzNb; e += blockDim.x) X[e] = 0.0;
+        __syncthreads();
+        const bool ok = ozaki_tile_update(sm, &g.mapA, &g.mapW, X, (int)(t * kOzS * kOzNb),
+                                          (int)((int64_t)j * kOzS * kOzNb), g.rexp + t * kOzNb,
+                                          g.wexp + (size_t)j * kOzNb, g.timeout_ns, hook, Done{g, a});
+        if (ok) ozaki_split(X, sl, g.rexp + t * kOzNb);
+        return ok;
+    }
+    // C(i, k) -= L(i, j) L(k, j)^T on the tensor cores; with `defer` its last
+    // quarter is left to the next update (tagged with `word`).
+    template <class Hook>
+    static __device__ bool update_sub(const Args &g, const SchedArgs &a, int i, int k, int j, Smem &sm,
+                                      const Hook &hook, bool defer, uint64_t word, uint64_t t0) {
+        const int64_t ta = tile_index(i, j), tb = tile_index(k, j);
+        return ozaki_tile_update(sm, &g.mapA, &g.mapB, g.S.tile(i, k), (int)(ta * kOzS * kOzNb),
+                                 (int)(tb * kOzS * kOzNb), g.rexp + ta * kOzNb, g.rexp + tb * kOzNb, g.timeout_ns,
+                                 hook, Done{g, a}, defer, word, t0);
+    }
 
     static __device__ void run(const Args &g, const SchedArgs &a, int m, int I, int K, int J, Smem &sm) {
         const int type = task_type(I, K, J);
         uint64_t t0 = 0;
         if (a.trace && threadIdx.x == 0) t0 = global_ns();
-        const TileStore<double> &S = g.S;
-        SimtSmem<double> &ss = *reinterpret_cast<SimtSmem<double> *>(sm.B);
         // the TMA producer (thread 0) takes the next task from the queues once
         // its loads are issued, while the tensor cores and the epilogue finish
         const auto take_ahead = [&a]() { df_take_ahead(a); };
+        const OzNoHook no_hook;
+        const int r = g.r, Mp = g.S.M;
+        const bool df = a.dfl != nullptr;
+        bool ok = true;
         if (!(a.flags & CHOL_FLAG_NOOP)) {
             switch (type) {
             case T_POTRF: {
-                const int li = oz_potrf128(S.tile(J, J), sm);
-                if (li) {
-                    if (threadIdx.x == 0) {
-                        report_info(a.ctl, (int64_t)J * kOzNb + li);
-                        st_release_s32(&a.ctl->abort, 1);
-                    }
-                } else if (J < S.M - 1) {
-                    // W_J = L_JJ^{-1} for the TRSMs of this block column, from
-                    // the factor still in shared memory; its slices (rows of W_J)
-                    // when it is well conditioned
-                    double *W = g.wbuf + (size_t)J * kOzNb * kOzNb;
-                    const double kappa = oz_trtri128(sm, W);
-                    const bool use_w = kappa <= kTrsmKappa;  // false also for a NaN
-                    if (use_w)
-                        ozaki_split(W, g.wslices + (size_t)J * kOzS * kOzNb * kOzNb, g.wexp + (size_t)J * kOzNb);
-                    if (threadIdx.x == 0) g.wflag[J] = use_w ? 1 : 0;
+                // right-looking over the subtiles of the diagonal tile
+                for (int c = 0; c < r && ok; ++c) {
+                    const int j = J * r + c;
+                    if (j >= Mp) break;
+                    if (!potrf_sub(g, a, j, sm)) break;  // info reported
+                    for (int q = c + 1; q < r && ok; ++q)
+                        if (J * r + q < Mp) ok = trsm_sub(g, a, J * r + q, j, sm, no_hook);
+                    for (int q = c + 1; q < r && ok; ++q)
+                        for (int p = c + 1; p <= q && ok; ++p)
+                            if (J * r + q < Mp) ok = update_sub(g, a, J * r + q, J * r + p, j, sm, no_hook, df,
+                                                                kOzNoTask, 0);
+                    if (ok) ok = flush_sub(g, a, sm);
                 }
             } break;
             case T_TRSM: {
-                if (!__ldcg(g.wflag + J)) {  // substitution on the CUDA cores (threads 0..255)
-                    if (threadIdx.x < kThreads) tile_trsm(S.tile(I, J), S.tile(J, J), kOzNb, ss);
-                    __syncthreads();
-                    const int64_t t = tile_index(I, J);
-                    ozaki_split(S.tile(I, J), g.slices + (size_t)t * kOzS * kOzNb * kOzNb, g.rexp + t * kOzNb);
+                if (r == 1) {
+                    ok = trsm_sub(g, a, I, J, sm, take_ahead);
                     break;
                 }
-                // A_IJ L_JJ^{-T} = A_IJ W_J^T on the tensor cores: the slices of
-                // -A_IJ go to this tile's slice slot, the tile is cleared, the
-                // emulated update C -= (-A_IJ) W_J^T leaves the solution in it,
-                // and the solution's own slices replace those of -A_IJ.
-                const int64_t t = tile_index(I, J);
-                double *X = S.tile(I, J);
-                __nv_bfloat16 *sl = g.slices + (size_t)t * kOzS * kOzNb * kOzNb;
-                ozaki_split(X, sl, g.rexp + t * kOzNb, true, false);
-                for (int e = threadIdx.x; e < kOzNb * kOzNb; e += blockDim.x) X[e] = 0.0;
-                __syncthreads();
-                const bool ok = ozaki_tile_update(sm, &g.mapA, &g.mapW, X, (int)(t * kOzS * kOzNb),
-                                                  (int)((int64_t)J * kOzS * kOzNb), g.rexp + t * kOzNb,
-                                                  g.wexp + (size_t)J * kOzNb, g.timeout_ns, take_ahead, Done{g, a});
-                if (ok) {
-                    ozaki_split(X, sl, g.rexp + t * kOzNb);
-                } else if (threadIdx.x == 0) {
-                    if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 4;
-                    st_release_s32(&a.ctl->abort, 1);
+                // per subtile column c of block column J: the TRSMs of the
+                // block row's subtiles, then their updates of the columns right
+                // of c inside the tile
+                for (int c = 0; c < r && ok; ++c) {
+                    const int j = J * r + c;
+                    for (int q = 0; q < r && ok; ++q) {
+                        if (I * r + q >= Mp) break;
+                        ok = trsm_sub(g, a, I * r + q, j, sm, no_hook);
+                    }
+                    for (int q = 0; q < r && ok; ++q)
+                        for (int p = c + 1; p < r && ok; ++p) {
+                            if (I * r + q >= Mp) break;
+                            ok = update_sub(g, a, I * r + q, J * r + p, j, sm, no_hook, df, kOzNoTask, 0);
+                        }
+                    if (ok) ok = flush_sub(g, a, sm);
                 }
             } break;
             default: {
-                const int64_t ta = tile_index(I, J), tb = tile_index(K, J);
-                const bool ok = ozaki_tile_update(sm, &g.mapA, &g.mapB, S.tile(I, K), (int)(ta * kOzS * kOzNb),
-                                                  (int)(tb * kOzS * kOzNb), g.rexp + ta * kOzNb,
-                                                  g.rexp + tb * kOzNb, g.timeout_ns, take_ahead, Done{g, a},
-                                                  a.dfl != nullptr, pack_task(m, I, K, J), t0);
-                if (!ok && threadIdx.x == 0) {
-                    if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 4;
-                    st_release_s32(&a.ctl->abort, 1);
-                }
+                // SYRK (K == I: the subtiles on or below the diagonal) or GEMM;
+                // subtile column c of J outermost, so each subtile receives
+                // its updates in ascending column; the task's last update
+                // defers its last quarter (the task completes with it)
+                int last_q = -1, last_p = -1;
+                for (int q = 0; q < r; ++q)
+                    for (int p = 0; p < r; ++p)
+                        if (I * r + q < Mp && K * r + p < Mp && (I != K || p <= q)) last_q = q, last_p = p;
+                for (int c = 0; c < r && ok; ++c)
+                    for (int q = 0; q < r && ok; ++q) {
+                        if (I * r + q >= Mp) break;
+                        for (int p = 0; p < r && ok; ++p) {
+                            if (K * r + p >= Mp || (I == K && p > q)) break;
+                            if (c == r - 1 && q == last_q && p == last_p)
+                                ok = update_sub(g, a, I * r + q, K * r + p, J * r + c, sm, take_ahead, df,
+                                                pack_task(m, I, K, J), t0);
+                            else
+                                ok = update_sub(g, a, I * r + q, K * r + p, J * r + c, sm, no_hook, df, kOzNoTask, 0);
+                        }
+                    }
             } break;
             }
         }
+        if (!ok && threadIdx.x == 0) fail_timeout(a);
         __syncthreads();
         if (threadIdx.x == 0 && !sm.os.pend) task_done_bookkeeping(a, type, m, I, K, J, t0);
     }
@@ -294,10 +381,15 @@ size_t fp64tc_extra_bytes(int64_t n) {
            a256((size_t)M * kOzNb * kOzNb * 8) + a256((size_t)M * 4);               // L_JJ^{-T}, flags
 }
 
-// Run the schedule with the tensor-core FP64 body on a repacked tile store.
-int fp64tc_schedule(double *store, int64_t n, Control *ctl, unsigned long long *queue, int32_t *deps, int sched,
-                    const chol_opts &o, cudaStream_t st, int *launches, cudaEvent_t e0) {
+// Run the schedule with the tensor-core FP64 body on a store repacked at
+// tile order 128; the tasks work on tiles of order nb = 128 r (Ml per
+// dimension), whose counters and queues the caller sized.
+int fp64tc_schedule(double *store, int64_t n, int64_t nb, Control *ctl, unsigned long long *queue, int32_t *deps,
+                    int sched, const chol_opts &o, cudaStream_t st, int *launches, cudaEvent_t e0) {
+    CHOL_CHECK_ARG(nb >= kOzNb && nb % kOzNb == 0, "the tensor-core FP64 engine takes tile orders 128 r");
     const int64_t M = (n + kOzNb - 1) / kOzNb;
+    const int r = (int)(nb / kOzNb);
+    const int64_t Ml = (M + r - 1) / r;
     const int64_t tiles = num_tiles(M);
     const size_t b_sl = a256((size_t)tiles * kOzS * kOzNb * kOzNb * 2);
     CHOL_CHECK_ARG(tiles * kOzS * kOzNb < (1ll << 31), "matrix too large for the slice maps");
@@ -318,6 +410,8 @@ int fp64tc_schedule(double *store, int64_t n, Control *ctl, unsigned long long *
     p += a256((size_t)M * kOzNb * kOzNb * 8);
     g.wflag = (int32_t *)p;
     g.timeout_ns = (uint64_t)(o.timeout_s * 1e9);
+    g.r = r;
+    g.Ml = (int32_t)Ml;
     int rc = make_slice_map(&g.mapA, g.slices, tiles * kOzS * kOzNb, 128);
     if (rc == CHOL_OK) rc = make_slice_map(&g.mapB, g.slices, tiles * kOzS * kOzNb, kOzQ);
     if (rc == CHOL_OK) rc = make_slice_map(&g.mapW, g.wslices, M * kOzS * kOzNb, kOzQ);
@@ -327,12 +421,12 @@ int fp64tc_schedule(double *store, int64_t n, Control *ctl, unsigned long long *
             DFArgs d{};
             d.queue = queue;
             d.deps = deps;
-            d.capacity = num_tasks(M);
-            d.total = num_tasks(M);
+            d.capacity = num_tasks(Ml);
+            d.total = num_tasks(Ml);
             d.num_matrices = 1;
             rc = launch_dataflow<OzBody>(g, a, d, o, st, launches, e0);
         } else {
-            rc = run_fork_join<OzBody>(g, a, (int)M, fj_variant(sched), st, launches, e0, o.timeout_s);
+            rc = run_fork_join<OzBody>(g, a, (int)Ml, fj_variant(sched), st, launches, e0, o.timeout_s);
         }
     }
     cudaFreeAsync(ws, st);

@@ -33,6 +33,7 @@ int fp64_solve_store(const double *store, int64_t n, int64_t nb, double *X, int6
                      cudaStream_t st, double timeout_s);
 size_t fp64_store_bytes(int64_t n, int64_t nb);
 size_t fp64tc_extra_bytes(int64_t n);
+bool fp64_uses_tc(int64_t n, int64_t nb, int32_t flags);
 size_t mixed_residual_keep_bytes(int64_t n);
 size_t mixed_residual_ws_bytes(int64_t n, int64_t nrhs);
 }  // namespace chol
@@ -77,8 +78,7 @@ int64_t tasks_of(int64_t M) { return M * (M + 1) * (M + 2) / 6; }
 // Measured single factorizations (dataflow): n = 1024 3.5 ms on both engines,
 // n = 1536 5.5 against 8.2 ms, n = 4096 15.6 against 31.5 ms.  A pure function
 // of n, so a request gives the same bits alone and in a mix.
-constexpr int64_t kServeTcMinN = 1024;
-bool fp64_on_tensor_cores(int64_t n) { return n > kServeTcMinN; }
+bool fp64_on_tensor_cores(int64_t n) { return chol::fp64_uses_tc(n, 0, 0); }
 int64_t fp64_nb(int64_t n) { return fp64_on_tensor_cores(n) ? 128 : chol_default_nb(n, CHOL_FP64); }
 
 // upper bound of the device bytes a request needs while it runs

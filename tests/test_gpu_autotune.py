@@ -7,7 +7,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec,cands", [("fp64", {32, 64, 128, 256, 512}), ("fp32", {128, 256, 512})])
+@pytest.mark.parametrize("prec,cands", [("fp64", {32, 64, 128, 256, 512, 1024}), ("fp32", {128, 256, 512})])
 def test_autotune_picks_a_candidate_and_caches(tmp_path, prec, cands):
     import paper_2606_11937_gb300 as chol
     path = str(tmp_path / "tune.json")

@@ -61,8 +61,10 @@ def test_batched_fp64_matches_solo_and_oracle(cap):
 
 
 def _solo(A, nb):
+    import paper_2606_11937_gb300 as chol
     from gpu_common import gpu_factor
-    return gpu_factor(A, schedule="dataflow", nb=nb)
+    # the batched FP64 bodies are the DFMA ones: compare with that engine
+    return gpu_factor(A, schedule="dataflow", nb=nb, flags=chol.CHOL_FLAG_FP64_SIMT)
 
 
 def test_batched_failure_is_isolated_and_graph_replays():
