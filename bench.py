@@ -1,13 +1,13 @@
 """Benchmark of the GB300 tiled Cholesky library; prints ONE JSON line.
 
 Default workload (one "step" = one full factorization A = L L^T through the
-C ABI): FP64, n = 32768, squared-exponential covariance of n points uniform in
+C ABI): FP64, n = 65536, squared-exponential covariance of n points uniform in
 the unit square (lengthscale 0.1, nugget 1e-2, seed 1), dataflow schedule with
 the priority queue, SYRK/GEMM on the tensor cores with binary64 accuracy
 (exact bf16 slicing; --flags 0 selects the DFMA engine).  Metric: TFLOP/s
 counting n^3/3 flops per factorization.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 32768] [--nb 256]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 65536] [--nb 128]
                   [--schedule dataflow|fork_join|fork_join_naive]
                   [--workload fp64|mixed|batched|serve] [--impl ours|reference]
 
@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
-    p.add_argument("--n", type=int, default=32768)
+    p.add_argument("--n", type=int, default=65536)
     p.add_argument("--nb", type=int, default=0)
     p.add_argument("--schedule", default="dataflow")
     p.add_argument("--workload", default="fp64", choices=["fp64", "mixed", "batched", "serve", "sweep"])
@@ -242,7 +242,7 @@ def run_fp64(args, world, rank, local):
     dev = torch.device("cuda", local)
     n = args.n
     tc = bool(args.flags & chol.CHOL_FLAG_FP64_TC)
-    nb = 128 if tc else (args.nb or chol.chol_default_nb(n, "fp64"))
+    nb = args.nb or (128 if tc else chol.chol_default_nb(n, "fp64"))
     A0 = si.se_covariance_torch(n, seed=1, lengthscale=0.1, nugget=1e-2, device=dev).T  # column-major view
     A = torch.empty_strided((n, n), (1, n), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -288,15 +288,19 @@ def run_fp64(args, world, rank, local):
         # measured sustained bf16 rate / 36 (POTRF/TRSM stay on the FP64 pipe).
         bf16 = measured_peaks().get("bf16_tflops_sustained", 1675.7)
         peak = bf16 / 36.0
-        # DRAM bytes (read + write) of one df_kernel<OzBody> launch at the
-        # default configuration (n = 32768, nb = 128, dataflow + priority),
-        # from one single-pass ncu capture of this kernel (1.180 TB read,
-        # 0.361 TB written); only for that configuration
-        default_cfg = (args.n == 32768 and nb == 128 and args.schedule == "dataflow" and args.flags == 18
-                       and args.num_ctas == 0)
-        traffic = 1.541e12 if default_cfg else None
+        # DRAM bytes (read + write) of the dataflow kernel per task, measured
+        # by ncu on a small case of the same configuration (n = 12288, nb = 128,
+        # dataflow + priority: 26.43 GB read + 20.16 GB written over 152 096
+        # tasks = 306.3 KB per task), scaled by this launch's task count.  Per-task
+        # DRAM bytes grow with n as block columns outgrow L2 (251 KB at n = 8192,
+        # 306 KB at 12288, 545 KB measured at 32768), so this is a lower bound.
+        same_cfg = nb == 128 and args.schedule == "dataflow" and args.flags == 18 and args.num_ctas == 0
+        m = -(-n // nb)
+        traffic = 306.3e3 * (m * (m + 1) * (m + 2) // 6) if same_cfg else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "df_kernel<OzBody>" if args.schedule == "dataflow" else "fork-join kernels",
+                "traffic": traffic, "traffic_source": "ncu DRAM bytes per task at n=12288 scaled by the task count "
+                                                      "(lower bound)" if traffic else None,
+                "kernel": "df_kernel<OzBody>" if args.schedule == "dataflow" else "fork-join kernels",
                 "peak_source": f"measured sustained bf16 {bf16} TFLOP/s / 36 slice products (FP64-equivalent)",
                 "fp64_pipe_peak": FP64_PEAK_TFLOPS}
     else:
