@@ -12,6 +12,12 @@
 //    that the CTAs pop.  No barrier ends a step.  Each tile receives its
 //    updates in ascending J (the chain dependency), exactly as under
 //    fork-join, so the two schedules produce identical bits.
+#include <atomic>
+#include <chrono>
+#include <functional>
+#include <mutex>
+#include <thread>
+
 #include "common.cuh"
 #include "factor_impl.cuh"
 
@@ -19,8 +25,16 @@ namespace chol {
 
 template struct TileStore<double>;
 
+// Early output of the dataflow schedule on the tensor-core engine (fp64tc.cu).
+struct EarlyOut {
+    double *out;
+    int64_t ld;
+    int32_t *cnt;
+    int32_t *flag;
+};
 int fp64tc_schedule(double *store, int64_t n, int64_t nb, Control *ctl, unsigned long long *queue, int32_t *deps,
-                    int sched, const chol_opts &o, cudaStream_t st, int *launches, cudaEvent_t e0);
+                    int sched, const chol_opts &o, cudaStream_t st, int *launches, cudaEvent_t e0,
+                    const EarlyOut *eo);
 
 // The FP64 engine a call runs, a pure function of (n, nb, flags): the
 // tensor-core engine (SYRK/GEMM/TRSM as exact bf16 slice products) when asked
@@ -49,7 +63,8 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // optionally unpack the factor into A_out, read back the control block and
 // synchronize.
 static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o, double *store, int64_t nb,
-                     int64_t tc_nb, int64_t *info, chol_stats *stats, double *A_out, int64_t lda_out) {
+                     int64_t tc_nb, int64_t *info, chol_stats *stats, double *A_out, int64_t lda_out,
+                     const EarlyOut *eo = nullptr, const std::function<void(cudaEvent_t)> *while_running = nullptr) {
     const int64_t M = (n + nb - 1) / nb;
     const int sched = o.schedule == CHOL_SCHED_AUTO ? CHOL_SCHED_DATAFLOW : o.schedule;
     CHOL_CHECK_ARG(sched >= CHOL_SCHED_FORK_JOIN && sched <= CHOL_SCHED_TOP_LOOKING, "unknown schedule");
@@ -78,7 +93,8 @@ static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o
         TileStore<double> S{ws.store, (int32_t)nb, (int32_t)M};
         SchedArgs a{ws.ctl, o.trace, o.trace_capacity, o.flags, 0};
         if (tc_nb) {
-            rc = fp64tc_schedule(ws.store, n, tc_nb, ws.ctl, ws.queue, ws.deps, sched, o, st, &launches, e0);
+            rc = fp64tc_schedule(ws.store, n, tc_nb, ws.ctl, ws.queue, ws.deps, sched, o, st, &launches, e0,
+                                 sched == CHOL_SCHED_DATAFLOW ? eo : nullptr);
         } else if (sched == CHOL_SCHED_DATAFLOW) {
             rc = run_dataflow<double>(S, a, ws.queue, ws.deps, o, st, &launches, e0);
         } else {
@@ -86,7 +102,14 @@ static int fp64_core(int64_t n, const double *A, int64_t lda, const chol_opts &o
         }
         if (rc != CHOL_OK) break;
         cudaEventRecord(e1, st);
-        if (A_out && (rc = launch_unpack<double, double>(ws.store, (int)nb, M, A_out, lda_out, n, st)) != CHOL_OK) break;
+        // (with early output the dataflow kernel already wrote every final tile)
+        if (A_out && !(eo && tc_nb && sched == CHOL_SCHED_DATAFLOW) &&
+            (rc = launch_unpack<double, double>(ws.store, (int)nb, M, A_out, lda_out, n, st)) != CHOL_OK)
+            break;
+        // work of the caller that overlaps the schedule (e1: the schedule's
+        // end); before the readback below, whose copy into pageable memory
+        // blocks this thread until the stream gets there
+        if (while_running) (*while_running)(e1);
         if (cudaMemcpyAsync(&h, ws.ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "readback", __FILE__, __LINE__); break; }
         if (cudaStreamSynchronize(st) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "sync", __FILE__, __LINE__); break; }
     } while (0);
@@ -132,7 +155,8 @@ static int check_tc_nb(int64_t nb) {
 }
 
 static int factor_fp64_device(int64_t n, double *A, int64_t lda, const chol_opts &o, int64_t *info,
-                              chol_stats *stats) {
+                              chol_stats *stats, const EarlyOut *eo = nullptr,
+                              const std::function<void(cudaEvent_t)> *while_running = nullptr) {
     const bool tc = fp64_uses_tc(n, o.nb, o.flags);
     const int64_t tnb = task_nb(n, o, tc);
     CHOL_CHECK_ARG(tnb >= 1 && tnb <= 2048, "nb must be in [1, 2048]");
@@ -143,7 +167,7 @@ static int factor_fp64_device(int64_t n, double *A, int64_t lda, const chol_opts
     prepare_pool();
     double *store = nullptr;
     CHOL_CUDA(cudaMallocAsync((void **)&store, fp64_store_bytes(n, nb), st));
-    const int rc = fp64_core(n, A, lda, o, store, nb, tc ? tnb : 0, info, stats, A, lda);
+    const int rc = fp64_core(n, A, lda, o, store, nb, tc ? tnb : 0, info, stats, A, lda, eo, while_running);
     cudaFreeAsync(store, st);
     return rc;
 }
@@ -223,39 +247,99 @@ int chol_factor_host(int64_t n, double *A_host, int64_t lda, const chol_opts *op
     if (n == 0) return CHOL_OK;
     CHOL_CHECK_ARG(A_host != nullptr, "A is NULL");
     chol_opts o = resolve_opts(opts);
+    CHOL_CHECK_ARG(o.precision == CHOL_FP64, "chol_factor_host computes in FP64");
     cudaStream_t st = (cudaStream_t)o.stream;
+    cudaGetLastError();  // errors left by earlier, unrelated runtime calls are not ours to report
     prepare_pool();
     double *dA = nullptr;
     CHOL_CUDA(cudaMallocAsync(&dA, (size_t)n * n * sizeof(double), st));
     int rc = CHOL_OK;
-    // only the lower triangle travels: per block of kCopyCols columns, rows
-    // j0 .. n-1 (the few entries above the diagonal inside a block's diagonal
+    // only the lower triangle travels: per block of columns from c0, rows
+    // c0 .. n-1 (the few entries above the diagonal inside a block's diagonal
     // square come along; the factorization never reads them, and on the way
     // back they are the caller's own values)
-    constexpr int64_t kCopyCols = 512;
-    auto copy_lower = [&](double *dst, int64_t ldd, const double *src, int64_t lds, cudaMemcpyKind kind) {
-        for (int64_t j0 = 0; j0 < n; j0 += kCopyCols) {
-            const int64_t w = n - j0 < kCopyCols ? n - j0 : kCopyCols;
+    auto copy_lower = [&](double *dst, int64_t ldd, const double *src, int64_t lds, cudaMemcpyKind kind, int64_t c0,
+                          int64_t c1, int64_t bw, cudaStream_t s) {
+        for (int64_t j0 = c0; j0 < c1; j0 += bw) {
+            const int64_t w = c1 - j0 < bw ? c1 - j0 : bw;
             const cudaError_t e = cudaMemcpy2DAsync(dst + j0 * ldd + j0, ldd * sizeof(double), src + j0 * lds + j0,
                                                     lds * sizeof(double), (size_t)(n - j0) * sizeof(double), (size_t)w,
-                                                    kind, st);
+                                                    kind, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     };
-    do {
-        if (copy_lower(dA, n, A_host, lda, cudaMemcpyHostToDevice) != cudaSuccess) {
-            rc = cuda_fail(cudaGetLastError(), "H2D", __FILE__, __LINE__);
-            break;
+    constexpr int64_t kCopyCols = 512;
+    if (copy_lower(dA, n, A_host, lda, cudaMemcpyHostToDevice, 0, n, kCopyCols, st) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "H2D", __FILE__, __LINE__);
+        cudaFreeAsync(dA, st);
+        return rc;
+    }
+    // The dataflow schedule on the tensor-core engine writes each tile of
+    // the factor to dA as soon as it is final and, once a block column is
+    // complete, sets that column's flag in page-locked host memory.  This
+    // thread polls the flags while the schedule runs and queues each
+    // column's copy back on a copy stream, so the copies overlap the
+    // factorization; whatever is not flagged when the schedule ends is copied
+    // then.  Other schedules and engines copy back after the factorization.
+    const int sched = o.schedule == CHOL_SCHED_AUTO ? CHOL_SCHED_DATAFLOW : o.schedule;
+    const bool tc = fp64_uses_tc(n, o.nb, o.flags);
+    const int64_t tnb = task_nb(n, o, tc);
+    const int64_t Mt = (n + tnb - 1) / tnb;
+    bool early = tc && sched == CHOL_SCHED_DATAFLOW && !(o.flags & CHOL_FLAG_NOOP) && tnb % 128 == 0 &&
+                 tnb <= kFp64TcMaxNb;
+    int32_t *cnt = nullptr, *hflag = nullptr, *dflag = nullptr;
+    cudaStream_t cs = nullptr;
+    if (early) {
+        early = cudaMallocAsync(&cnt, (size_t)Mt * sizeof(int32_t), st) == cudaSuccess &&
+                cudaMemsetAsync(cnt, 0, (size_t)Mt * sizeof(int32_t), st) == cudaSuccess &&
+                cudaHostAlloc(&hflag, (size_t)Mt * sizeof(int32_t), cudaHostAllocMapped) == cudaSuccess &&
+                cudaHostGetDevicePointer((void **)&dflag, hflag, 0) == cudaSuccess &&
+                cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+        if (!early) cudaGetLastError();
+    }
+    if (early) {
+        for (int64_t K = 0; K < Mt; ++K) reinterpret_cast<volatile int32_t *>(hflag)[K] = 0;
+        EarlyOut eo{dA, n, cnt, dflag};
+        cudaError_t ce = cudaSuccess;
+        const std::function<void(cudaEvent_t)> overlap = [&](cudaEvent_t sched_end) {
+            // the schedule was enqueued on st after the flags were cleared;
+            // queue each block column's copy once its flag is set, the rest
+            // once the schedule has ended (its end event is recorded on st)
+            int64_t next = 0;
+            while (next < Mt && ce == cudaSuccess) {
+                // (any answer but "not ready", an error included, ends the polling)
+                const bool ended = cudaEventQuery(sched_end) != cudaErrorNotReady;
+                int64_t upto = next;
+                while (upto < Mt && (ended || reinterpret_cast<volatile int32_t *>(hflag)[upto] != 0)) ++upto;
+                if (upto > next) {
+                    std::atomic_thread_fence(std::memory_order_acquire);
+                    if (ended) ce = cudaStreamWaitEvent(cs, sched_end, 0);  // the rest: after the schedule
+                    if (ce == cudaSuccess)
+                        ce = copy_lower(A_host, lda, dA, n, cudaMemcpyDeviceToHost, next * tnb,
+                                        upto * tnb < n ? upto * tnb : n, tnb, cs);
+                    next = upto;
+                } else {
+                    std::this_thread::sleep_for(std::chrono::microseconds(50));
+                }
+            }
+        };
+        rc = factor_fp64_device(n, dA, n, o, info, stats, &eo, &overlap);
+        if (cudaStreamSynchronize(cs) != cudaSuccess || ce != cudaSuccess) {
+            if (rc == CHOL_OK) rc = cuda_fail(ce != cudaSuccess ? ce : cudaGetLastError(), "D2H", __FILE__, __LINE__);
         }
-        if ((rc = chol_factor_ex(n, dA, n, &o, info, stats)) != CHOL_OK) break;
-        if (copy_lower(A_host, lda, dA, n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    } else {
+        rc = chol_factor_ex(n, dA, n, &o, info, stats);
+        if (rc == CHOL_OK && copy_lower(A_host, lda, dA, n, cudaMemcpyDeviceToHost, 0, n, kCopyCols, st) != cudaSuccess)
             rc = cuda_fail(cudaGetLastError(), "D2H", __FILE__, __LINE__);
-            break;
-        }
-        if (cudaStreamSynchronize(st) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "sync", __FILE__, __LINE__);
-    } while (0);
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc == CHOL_OK)
+            rc = cuda_fail(cudaGetLastError(), "sync", __FILE__, __LINE__);
+    }
+    if (cnt) cudaFreeAsync(cnt, st);
     cudaFreeAsync(dA, st);
+    cudaStreamSynchronize(st);
+    if (cs) cudaStreamDestroy(cs);
+    if (hflag) cudaFreeHost(hflag);
     return rc;
 }
 

@@ -18,6 +18,8 @@
 //   static __device__ void solve(const Args &, const SchedArgs &, int m, Smem &);
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "simt_tiles.cuh"
 
@@ -64,6 +66,14 @@ struct DFLocal {
 };
 
 constexpr int kSolveJ = 0xFFFF;  // J marker of the fused SOLVE task (batched)
+
+// Optional body hook, run by the dataflow kernel with all threads once a
+// tile's final task (POTRF or TRSM) has completed and released its
+// successors: Body::kFinalHook and Body::final_hook(g, a, m, I, K, sm).
+template <class B, class = void>
+struct BodyFinalHook : std::false_type {};
+template <class B>
+struct BodyFinalHook<B, std::void_t<decltype(B::kFinalHook)>> : std::integral_constant<bool, B::kFinalHook> {};
 
 // ----------------------------------------------------------------- repack / unpack
 // (I, K) of lower tile index t = I (I + 1) / 2 + K
@@ -791,6 +801,12 @@ __global__ void __launch_bounds__(Body::kBlock) df_kernel(const __grid_constant_
             }
         } else if (threadIdx.x == 0 && lagged) {
             aborted = ld_relaxed_s32(&ctl->abort);
+        }
+        if constexpr (BodyFinalHook<Body>::value) {
+            if (J == K) {  // POTRF / TRSM: tile (I, K) is final
+                __syncthreads();
+                Body::final_hook(g, a, m, I, K, sm);
+            }
         }
     }
     Body::cta_fini(g, sm);

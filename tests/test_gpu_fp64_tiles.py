@@ -233,3 +233,30 @@ def test_withheld_dependency_times_out_at_tile_order_256():
     Lref, _ = oracle_factor("gram", 2048, 1)
     L, info, st, rc = gpu_factor(A, schedule="dataflow", nb=256)
     assert rc == 0 and scaled_error(L, Lref, A) <= TOL_SCALED
+
+
+@pytest.mark.parametrize("sched", ["dataflow", "fork_join"])
+def test_host_buffer_not_spd_and_schedules(sched):
+    """The host-buffer call on this engine: with the dataflow schedule each
+    block column is copied back as soon as it is final (a copy stream waits on
+    per-column flags); a matrix that is not positive definite still returns
+    (every flag is released after the schedule) with the oracle's info, and
+    the fork-join schedule copies back after the factorization."""
+    import torch
+
+    import oracle
+    import paper_2606_11937_gb300 as chol
+    n = 1300
+    A = matrix("gram", n, 9)
+    Lref, _ = oracle_factor("gram", n, 9)
+    for nb in (128, 256):
+        h = torch.from_numpy(np.asfortranarray(A)).T.contiguous().T.pin_memory()
+        info, st = chol.chol_factor_host(h, chol.opts(nb=nb, schedule=sched))
+        assert info == 0
+        assert scaled_error(h.numpy(), Lref, A) <= TOL_SCALED
+    B = A.copy()
+    B[900, 900] -= 1000.0
+    _, want = oracle.potrf_unblocked(B)
+    h = torch.from_numpy(np.asfortranarray(B)).T.contiguous().T.pin_memory()
+    info, st = chol.chol_factor_host(h, chol.opts(nb=128, schedule=sched))
+    assert info == want == 901
