@@ -101,8 +101,15 @@ def run_mixed(args, world, rank, local):
     h.solve(B, raise_on_error=False)
     torch.cuda.synchronize()
     solve_again_s = time.perf_counter() - t
+    Lm = None if args.no_fp64_compare else h.factor()
     h.close()
-    fp64 = None if args.no_fp64_compare else _fp64_time_to_solution(A, B, stream, chol)
+    fp64, factor_err = None, None
+    if not args.no_fp64_compare:
+        fp64, L64 = _fp64_time_to_solution(A, B, stream, chol, keep_factor=True)
+        # the low-precision factor against the FP64 one (whose own residual
+        # the FP64 parity tests bound): max_{i>=j} |L_ij - L64_ij| / sqrt(A_ii)
+        factor_err = _scaled_factor_error(Lm, L64, A)
+        del Lm, L64
     ms = bench.allreduce_max(statistics.mean(times), world)
     value = world * flops / (ms / 1e3) / 1e12
     achieved = flops / (statistics.mean(kms) / 1e3) / 1e12
@@ -126,6 +133,7 @@ def run_mixed(args, world, rank, local):
                                               "solve_s": solve_s, "time_to_solution_s": ms / 1e3 + solve_s,
                                               "solve_again_s": solve_again_s},
                                "fp64_reference_path": fp64,
+                               "factor_error_vs_fp64": factor_err,
                                "clocks": clk.summary()})
         print(json.dumps(line), flush=True)
 
@@ -140,7 +148,20 @@ def _berr(A, X, B):
     return float(torch.max(num / den))
 
 
-def _fp64_time_to_solution(A, B, stream, chol):
+def _scaled_factor_error(L, Lref, A, blk: int = 4096) -> float:
+    """max_{i>=j} |L_ij - Lref_ij| / sqrt(A_ii) over column blocks (column-major n x n tensors)."""
+    import torch
+    n = A.shape[0]
+    scale = torch.sqrt(torch.diagonal(A)).reshape(n, 1)
+    err = 0.0
+    for c0 in range(0, n, blk):
+        c1 = min(n, c0 + blk)
+        d = torch.tril(L[:, c0:c1] - Lref[:, c0:c1], diagonal=-c0).abs() / scale
+        err = max(err, float(d.max()))
+    return err
+
+
+def _fp64_time_to_solution(A, B, stream, chol, keep_factor: bool = False):
     """The plain FP64 path on the same inputs: chol_factor_ex (tensor-core
     engine, exact slicing) + chol_solve_ex, device time, with its backward
     error; the second of two runs is reported."""
@@ -167,6 +188,8 @@ def _fp64_time_to_solution(A, B, stream, chol):
                "factor_s": e0.elapsed_time(e1) / 1e3, "solve_s": e1.elapsed_time(e2) / 1e3,
                "time_to_solution_s": e0.elapsed_time(e2) / 1e3}
     out["berr"] = _berr(A, X, B)
+    if keep_factor:
+        return out, L
     del L
     return out
 

@@ -180,12 +180,18 @@ int64_t chol_last_info(void);
 int chol_factor_ex(int64_t n, double *A, int64_t lda, const chol_opts *opts,
                    int64_t *info, chol_stats *stats);
 
-/* As chol_factor_ex, but A is a HOST buffer (pinned memory copies fastest):
- * the library copies the lower triangle to the device, factors it and copies
- * the lower triangle back (end-to-end path).  Each copy moves, per block of
- * 512 columns starting at column j0, rows j0 .. n-1 of those columns: the
- * lower triangle plus the upper part of each block's diagonal square, which
- * is written back unchanged. */
+/* As chol_factor_ex, but A is a HOST buffer (end-to-end path; page-locked
+ * memory copies fastest): the library copies the lower triangle to a device
+ * buffer of n x n elements, factors it and copies the lower triangle back.
+ * Each copy moves, per block of columns starting at column j0, rows j0 .. n-1
+ * of those columns: the lower triangle plus the upper part of each block's
+ * diagonal square, which is written back unchanged.  With the dataflow
+ * schedule on the tensor-core engine the copy back overlaps the
+ * factorization: the kernel writes each tile of the factor as soon as it is
+ * final and flags each complete block column (of order nb) in page-locked
+ * memory; the calling thread polls the flags and queues that column's copy on
+ * a copy stream of its own, and copies whatever is left when the schedule has
+ * ended.  The call returns after all copies. */
 int chol_factor_host(int64_t n, double *A_host, int64_t lda, const chol_opts *opts,
                      int64_t *info, chol_stats *stats);
 
