@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--noop", action="store_true")
     p.add_argument("--trace", action="store_true")
     p.add_argument("--batch-count", type=int, default=4096)
+    p.add_argument("--tc-min-order", type=int, default=0,
+                   help="batched FP64: order above which a matrix runs on the tensor cores (0 = 1024)")
     p.add_argument("--serve-requests", type=int, default=120)
     p.add_argument("--serve-rates", default="20,80,320")
     p.add_argument("--serve-nmax", type=int, default=8192)

@@ -66,26 +66,36 @@ def run_batched(args, world, rank, local):
     As = [torch.empty_strided((n, n), (1, n), dtype=torch.float64, device=dev) for n in ns]
     Bs = [torch.empty_like(b) for b in B0]
     prec = args.precision if args.precision in ("fp64", "fp32") else "fp64"
-    flags = chol.CHOL_FLAG_PRIORITY if args.flags & chol.CHOL_FLAG_PRIORITY else 0
     cap = args.nb
+    flags = args.flags & (chol.CHOL_FLAG_PRIORITY | chol.CHOL_FLAG_FP64_SIMT)
     tuned = None
     if cap == 0:
-        # autotune the tile-order cap on this batch (timed on the real plan)
-        best = None
+        # autotune on this batch, timed on the real plan: the tile-order cap of
+        # the CUDA-core bodies, the engine split (FP64: matrices above order
+        # 1024 on the tensor-core engine, or every matrix on the CUDA cores)
+        # and the priority order of the ready queue
+        # (engine split: (flags, order above which a matrix goes to the tensor cores))
+        engines = ([(0, 64), (0, 128), (0, 256), (0, 512), (0, 1024), (chol.CHOL_FLAG_FP64_SIMT, 0)]
+                   if prec == "fp64" else [(0, 0)])
+        trials = []
         for c in (32, 64, 128, 256):
-            plan = chol.chol_batch_plan(ns, chol.opts(nb=c, precision=prec, flags=flags))
-            for a, a0 in zip(As, A0):
-                a.copy_(a0)
-            for b, b0 in zip(Bs, B0):
-                b.copy_(b0)
-            plan.run(As, Bs)
-            ms = plan.stats().device_ms
-            plan.close()
-            if best is None or ms < best[1]:
-                best = (c, ms)
-        cap = best[0]
-        tuned = {"candidates": [32, 64, 128, 256], "chosen_cap": cap}
-    plan = chol.chol_batch_plan(ns, chol.opts(nb=cap, precision=prec, flags=flags))
+            for e, tmin in engines:
+                for pr in (0, chol.CHOL_FLAG_PRIORITY):
+                    plan = chol.chol_batch_plan(ns, chol.opts(nb=c, precision=prec, flags=e | pr, tc_min_order=tmin))
+                    for a, a0 in zip(As, A0):
+                        a.copy_(a0)
+                    for b, b0 in zip(Bs, B0):
+                        b.copy_(b0)
+                    plan.run(As, Bs)
+                    trials.append({"cap": c, "flags": e | pr, "tc_min_order": tmin, "ms": plan.stats().device_ms})
+                    plan.close()
+        best = min(trials, key=lambda t: t["ms"])
+        cap, flags, tc_min = best["cap"], best["flags"], best["tc_min_order"]
+        tuned = {"trials": trials, "chosen": best}
+    else:
+        tc_min = args.tc_min_order
+    plan = chol.chol_batch_plan(ns, chol.opts(nb=cap, precision=prec, flags=flags, tc_min_order=tc_min))
+    tc_part = prec == "fp64" and not (flags & chol.CHOL_FLAG_FP64_SIMT) and any(n > (tc_min or 1024) for n in ns)
     flops = sum(n ** 3 / 3.0 for n in ns)
     solve_flops = sum(2.0 * n * n for n in ns)
 
@@ -111,6 +121,7 @@ def run_batched(args, world, rank, local):
             kms.append(plan.stats().device_ms)
     bench.barrier(world)
     st = plan.stats()
+    check = _check_batch(As, Bs, A0, B0, ns, idx, prec) if rank == 0 else None
     ms = bench.allreduce_max(statistics.mean(times), world)
     total_flops = flops * world if world > 1 else flops  # shards are about equal; report the job total below
     if world > 1:
@@ -120,23 +131,67 @@ def run_batched(args, world, rank, local):
         total_flops = float(t.item())
     value = total_flops / (ms / 1e3) / 1e12
     achieved = flops / (statistics.mean(kms) / 1e3) / 1e12
-    peak = bench.FP64_PEAK_TFLOPS if prec == "fp64" else 78.3
+    # ceilings: the tensor-core part (most of the flops of an FP64 batch) against
+    # the exact-slicing ceiling (sustained bf16 / 36); CUDA-core bodies against
+    # the FP64 pipe or the FP32 FMA pipe (152 SMs x 128 lanes x 2 flop x 2.07 GHz)
+    if tc_part:
+        bound, peak = "tensor", bench.measured_peaks().get("bf16_tflops_sustained", 1704.0) / 36.0
+        kernel = "df_kernel<OzBatchBody> + df_kernel<BatchBody<double>>"
+    elif prec == "fp64":
+        bound, peak, kernel = "alu", bench.FP64_PEAK_TFLOPS, "df_kernel<BatchBody<double>>"
+    else:
+        bound, peak, kernel = "alu", 152 * 128 * 2 * 2.07e9 / 1e12, "df_kernel<BatchBody<float>>"
     if rank == 0:
         line = {"metric": bench.METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": f"batched factor+solve of {count} SPD systems, n log-uniform [32, 2048] "
                                        f"(seed 3), A_i = G_i G_i^T/n_i + I, 1 RHS each, {prec}, one graph launch",
-                           "batch": count, "tile_cap": cap, "precision": prec,
+                           "batch": count, "tile_cap": cap, "precision": prec, "flags": flags,
+                           "tensor_core_part": f"FP64 matrices of order above {tc_min or 1024}" if tc_part else None,
                            "sum_n3_over_3": flops, "parallelism": f"contiguous shards x{world}",
                            "l2": "inputs larger than L2"},
-                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "traffic": None,
-                             "kernel": f"df_kernel<BatchBody<{'double' if prec == 'fp64' else 'float'}>>"},
+                "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None, "kernel": kernel},
+                "check": check,
                 "solves_per_s": world * len(ns) / (ms / 1e3), "solve_flops": solve_flops, "tasks": list(st.tasks),
                 "autotune": tuned, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     plan.close()
+
+
+def _check_batch(As, Bs, A0, B0, ns, idx, prec, subset: int = 256, seed: int = 17):
+    """Every solution's normwise backward error, recomputed from the inputs
+    (torch, binary64), and the factor of a seeded subset of the matrices
+    against the oracle's unblocked factorization (host cores, in parallel)."""
+    import concurrent.futures as cf
+    import os
+
+    import torch
+
+    import oracle
+    berr = []
+    for a0, x, b0 in zip(A0, Bs, B0):
+        r = b0 - a0 @ x
+        den = torch.max(torch.sum(torch.abs(a0), dim=1)) * torch.max(torch.abs(x)) + torch.max(torch.abs(b0))
+        berr.append(float(torch.max(torch.abs(r)) / den))
+    rng = np.random.default_rng(seed)
+    pick = sorted(rng.choice(len(ns), size=min(subset, len(ns)), replace=False).tolist())
+    host = [(A0[k].cpu().numpy(), np.tril(As[k].cpu().numpy())) for k in pick]
+
+    def one(pair):
+        A, L = pair
+        Lref, info = oracle.potrf_unblocked(A)
+        scale = np.sqrt(np.diag(A))[:, None]
+        return float(np.max(np.abs(L - np.tril(Lref)) / scale)), info
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        res = list(ex.map(one, host))
+    tol_berr = 1e-14 if prec == "fp64" else 1e-6
+    tol_fac = 1e-11 if prec == "fp64" else 1e-5
+    return {"berr_max": max(berr), "berr_all_within": all(b <= tol_berr for b in berr), "berr_tol": tol_berr,
+            "oracle_subset": len(pick), "oracle_scaled_err_max": max(r[0] for r in res),
+            "oracle_all_within": all(r[0] <= tol_fac and r[1] == 0 for r in res), "oracle_tol": tol_fac}
 
 
 def run_serve(args, world, rank, local):

@@ -139,7 +139,9 @@ typedef struct {
     void *stream;           /* cudaStream_t; NULL = legacy default stream */
     int32_t num_ctas;       /* dataflow grid size; 0 = default (4 CTAs per SM for the CUDA-core
                                bodies, 1 per SM for the tensor-core body) */
-    int32_t reserved;
+    int32_t tc_min_order;   /* batched FP64 plans: matrices of order above this run on the tensor-core
+                               engine (0 = 1024, the order above which a single FP64 factorization
+                               uses it by default) */
     chol_trace_rec *trace;  /* device buffer of trace_capacity records, or NULL */
     int64_t trace_capacity;
 } chol_opts;
@@ -279,7 +281,13 @@ typedef struct chol_batch_s *chol_batch_h;
  * that is captured once into a CUDA graph and replayed by chol_batch_run.
  * precision: CHOL_FP64 or CHOL_FP32 (true binary32 arithmetic).  The tile
  * order of each matrix comes from the autotuner's table for its n (opts->nb
- * > 0 forces one nb for all). */
+ * > 0 forces one nb for all).  In FP64 plans the matrices of order above 1024
+ * (or above opts->tc_min_order) run on the tensor-core engine: tiles of order
+ * 128, all of them in one persistent kernel of their own, each with the bits
+ * of a single factorization of it with CHOL_FLAG_FP64_TC and nb = 128 (the
+ * default single factorization above order 1024); opts->nb applies to the
+ * others, and CHOL_FLAG_FP64_SIMT in opts->flags keeps every matrix on the
+ * CUDA-core bodies. */
 int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol_batch_h *out);
 
 /* Factor every A[i] in place (lower triangle <- L_i) and overwrite B[i] with
@@ -290,8 +298,9 @@ int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol
 int chol_batch_run(chol_batch_h plan, double *const *A, const int64_t *lda,
                    double *const *B, int64_t *info);
 
-/* Statistics of the last run: tasks executed (summed) and the device time of
- * the whole graph (repack, persistent factor+solve kernel, unpack). */
+/* Statistics of the last run: tasks executed (summed over both parts) and the
+ * device time of the whole graph (repack, the persistent factor+solve
+ * kernels, unpack). */
 int chol_batch_stats(chol_batch_h plan, chol_stats *stats);
 
 void chol_batch_free(chol_batch_h plan);

@@ -45,7 +45,7 @@ class chol_trace_rec(ctypes.Structure):
 class chol_opts(ctypes.Structure):
     _fields_ = [("schedule", _i32), ("precision", _i32), ("nb", _i64), ("flags", _i32), ("max_iter", _i32),
                 ("refine_tol", _dbl), ("timeout_s", _dbl), ("stream", _vp), ("num_ctas", _i32),
-                ("reserved", _i32), ("trace", _vp), ("trace_capacity", _i64)]
+                ("tc_min_order", _i32), ("trace", _vp), ("trace_capacity", _i64)]
 
 
 class chol_stats(ctypes.Structure):
@@ -176,7 +176,7 @@ def colmajor(x, device="cuda", dtype=None):
 
 
 def opts(schedule="auto", precision="fp64", nb=0, flags=0, max_iter=30, refine_tol=1e-14, timeout_s=60.0,
-         stream=None, num_ctas=0, trace=None, trace_capacity=0) -> chol_opts:
+         stream=None, num_ctas=0, trace=None, trace_capacity=0, tc_min_order=0) -> chol_opts:
     o = chol_opts()
     lib().chol_opts_init(ctypes.byref(o))
     o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
@@ -188,6 +188,7 @@ def opts(schedule="auto", precision="fp64", nb=0, flags=0, max_iter=30, refine_t
     o.timeout_s = float(timeout_s)
     o.stream = _stream() if stream is None else int(stream)
     o.num_ctas = int(num_ctas)
+    o.tc_min_order = int(tc_min_order)
     o.trace = _ptr(trace) or None
     o.trace_capacity = int(trace_capacity)
     return o

@@ -9,29 +9,19 @@
 // the forward and backward substitution for its right-hand side in one CTA.
 // The graph holds: descriptor upload (from pinned host memory), repack of all
 // matrices, queue/counter reset, queue seeding, the persistent kernel, unpack
-// of the factors and the info download.
+// of the factors and the info download.  In FP64 batches the matrices of
+// order above 1024 (where a single factorization runs on the tensor cores)
+// form a part of their own: tiles of order 128 and one persistent kernel of
+// the tensor-core engine for all of them (batched_tc.cu), before the
+// persistent kernel of the others; internally the smaller matrices come
+// first (a permutation maps them back to the caller's order).
 #include <string.h>
 
 #include <vector>
 
-#include "common.cuh"
-#include "factor_impl.cuh"
+#include "batched_impl.cuh"
 
 namespace chol {
-
-struct MatDesc {
-    void *store;        // tiles of this matrix (double or float)
-    int64_t task_base;  // offset of its task counters
-    double *A;          // caller's matrix (input, factor output)
-    int64_t lda;
-    double *b;          // caller's right-hand side (input, solution output)
-    int32_t n, nb, M, pad;
-};
-
-struct TileRef {
-    int32_t m;
-    int32_t t;  // lower tile index inside matrix m
-};
 
 template <typename T>
 struct BatchSmem {
@@ -95,36 +85,7 @@ struct BatchBody {
         const bool skip = (a.flags & CHOL_FLAG_NOOP) || ld_acquire_s32(g.failed + m);
         const int n = d.n, nb = d.nb;
         if (!skip) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) sm.y[i] = (T)d.b[i];
-            __syncthreads();
-            for (int k = 0; k < n; ++k) {
-                const T *Lk = tile(d, k / nb, k / nb);
-                if (threadIdx.x == 0) sm.y[k] = sm.y[k] / __ldcg(Lk + (size_t)(k % nb) * nb + k % nb);
-                __syncthreads();
-                const T yk = sm.y[k];
-                for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) {
-                    const T *t = tile(d, i / nb, k / nb);
-                    sm.y[i] = fma(-__ldcg(t + (size_t)(i % nb) * nb + k % nb), yk, sm.y[i]);
-                }
-                __syncthreads();
-            }
-            for (int k = n - 1; k >= 0; --k) {
-                // warp-parallel dot product over i > k of L(i, k) x_i
-                T s = T(0);
-                if (threadIdx.x < 32) {
-                    for (int i = k + 1 + threadIdx.x; i < n; i += 32) {
-                        const T *t = tile(d, i / nb, k / nb);
-                        s = fma(__ldcg(t + (size_t)(i % nb) * nb + k % nb), sm.y[i], s);
-                    }
-                    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                    if (threadIdx.x == 0) {
-                        const T *Lk = tile(d, k / nb, k / nb);
-                        sm.y[k] = (sm.y[k] - s) / __ldcg(Lk + (size_t)(k % nb) * nb + k % nb);
-                    }
-                }
-                __syncthreads();
-            }
-            for (int i = threadIdx.x; i < n; i += blockDim.x) d.b[i] = (double)sm.y[i];
+            tiles_solve<T>(reinterpret_cast<const T *>(d.store), nb, n, d.b, sm.y);
         }
         __syncthreads();
         if (threadIdx.x == 0 && a.trace) {
@@ -143,58 +104,6 @@ struct BatchBody {
     }
 };
 
-// Repack / unpack over a flat list of (matrix, tile); grid.y = 32 x 32 sub-block.
-template <typename T>
-__global__ void __launch_bounds__(256) batch_repack_kernel(const MatDesc *desc, const TileRef *list) {
-    __shared__ T buf[32][33];
-    const TileRef tr = list[blockIdx.x];
-    const MatDesc d = desc[tr.m];
-    const int nb = d.nb, nsb = (nb + 31) / 32;
-    if ((int)blockIdx.y >= nsb * nsb) return;
-    int I, K;
-    tile_of(tr.t, I, K);
-    const int sr = blockIdx.y / nsb, sc = blockIdx.y % nsb;
-    T *tile = reinterpret_cast<T *>(d.store) + (size_t)tr.t * nb * nb;
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
-        const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
-        T v = T(0);
-        if (r < nb && c < nb) {
-            if (i < d.n && j < d.n) v = j <= i ? (T)d.A[j * d.lda + i] : T(0);
-            else v = i == j ? T(1) : T(0);
-        }
-        buf[yy][threadIdx.x] = v;
-    }
-    __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
-        if (r < nb && c < nb) tile[(size_t)r * nb + c] = buf[threadIdx.x][yy];
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) batch_unpack_kernel(const MatDesc *desc, const TileRef *list) {
-    __shared__ T buf[32][33];
-    const TileRef tr = list[blockIdx.x];
-    const MatDesc d = desc[tr.m];
-    const int nb = d.nb, nsb = (nb + 31) / 32;
-    if ((int)blockIdx.y >= nsb * nsb) return;
-    int I, K;
-    tile_of(tr.t, I, K);
-    const int sr = blockIdx.y / nsb, sc = blockIdx.y % nsb;
-    const T *tile = reinterpret_cast<const T *>(d.store) + (size_t)tr.t * nb * nb;
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
-        buf[yy][threadIdx.x] = (r < nb && c < nb) ? tile[(size_t)r * nb + c] : T(0);
-    }
-    __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
-        const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
-        if (r < nb && c < nb && i < d.n && j < d.n && j <= i) d.A[j * d.lda + i] = (double)buf[threadIdx.x][yy];
-    }
-}
-
 }  // namespace chol
 
 using namespace chol;
@@ -202,7 +111,11 @@ using namespace chol;
 struct chol_batch_s {
     int32_t batch = 0;
     int32_t precision = CHOL_FP64;
-    std::vector<int64_t> n, nb, M;
+    std::vector<int64_t> n, nb, M;      // internal order: matrices of the CUDA-core part, then the tensor-core part
+    std::vector<int32_t> perm;          // perm[k] = caller's index of internal matrix k
+    int32_t small = 0;                  // matrices of the CUDA-core part
+    OzBatchPart *tc = nullptr;          // tensor-core part (matrices small .. batch-1), or null
+    void *tc_ws = nullptr;
     chol_opts opts{};
     int64_t total_tasks = 0, total_tiles = 0;
     int max_nsb2 = 1;
@@ -240,17 +153,28 @@ static int record_batch(chol_batch_s *p) {
     const dim3 rgrid((unsigned)p->total_tiles, (unsigned)p->max_nsb2);
     batch_repack_kernel<T><<<rgrid, dim3(32, 8), 0, st>>>(p->d_desc, p->d_list);
     CHOL_CUDA(cudaGetLastError());
-    typename BatchBody<T>::Args g{p->d_desc, p->d_info, p->d_failed};
-    SchedArgs a{p->d_ctl, p->opts.trace, p->opts.trace_capacity, p->opts.flags, 0};
-    DFArgs d{};
-    d.queue = p->d_queue;
-    d.deps = p->d_deps;
-    d.capacity = p->total_tasks;
-    d.total = p->total_tasks;
-    d.num_matrices = p->batch;
-    int launches = 0;
-    int rc = launch_dataflow<BatchBody<T>>(g, a, d, p->opts, st, &launches, p->e0);
-    if (rc != CHOL_OK) return rc;
+    int launches = 0, rc = CHOL_OK;
+    CHOL_CUDA(cudaEventRecord(p->e0, st));
+    if (p->tc) {
+        int l = 0;
+        if ((rc = oz_batch_record(p->tc, p->d_desc + p->small, p->d_info + p->small, p->d_failed + p->small, st,
+                                  &l)) != CHOL_OK)
+            return rc;
+        launches += l;
+    }
+    if (p->small > 0) {
+        typename BatchBody<T>::Args g{p->d_desc, p->d_info, p->d_failed};
+        SchedArgs a{p->d_ctl, p->opts.trace, p->opts.trace_capacity, p->opts.flags, 0};
+        DFArgs d{};
+        d.queue = p->d_queue;
+        d.deps = p->d_deps;
+        d.capacity = p->total_tasks;
+        d.total = p->total_tasks;
+        d.num_matrices = p->small;
+        int l = 0;
+        if ((rc = launch_dataflow<BatchBody<T>>(g, a, d, p->opts, st, &l)) != CHOL_OK) return rc;
+        launches += l;
+    }
     CHOL_CUDA(cudaEventRecord(p->e1, st));
     batch_unpack_kernel<T><<<rgrid, dim3(32, 8), 0, st>>>(p->d_desc, p->d_list);
     CHOL_CUDA(cudaGetLastError());
@@ -268,6 +192,8 @@ void chol_batch_free(chol_batch_h p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->ws) cudaFree(p->ws);
+    if (p->tc) oz_batch_destroy(p->tc);
+    if (p->tc_ws) cudaFree(p->tc_ws);
     if (p->h_desc) cudaFreeHost(p->h_desc);
     if (p->h_info) cudaFreeHost(p->h_info);
     if (p->h_ctl) cudaFreeHost(p->h_ctl);
@@ -300,14 +226,34 @@ int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol
             set_error("argument: batched orders must be in [1, 2048] (matrix %d has n=%lld)", i, (long long)n[i]);
             return CHOL_ERR_ARG;
         }
-        int64_t nb = o.nb > 0 ? o.nb : chol_default_nb(n[i], o.precision);
-        if (nb > n[i]) nb = n[i];  // a matrix smaller than the tile is one tile of its own order
-        const int64_t M = (n[i] + nb - 1) / nb;
-        p->n.push_back(n[i]);
+    }
+    // FP64 matrices above order 1024 (or opts->tc_min_order) go to the
+    // tensor-core part (1024: the choice of a single FP64 factorization with
+    // the default tile order); the others keep the CUDA-core bodies with the
+    // tile order (cap) of opts->nb
+    const int64_t tc_min = o.tc_min_order > 0 ? o.tc_min_order : kFp64TcMinN;
+    auto on_tc = [&](int64_t nn) {
+        return o.precision == CHOL_FP64 && !(o.flags & CHOL_FLAG_FP64_SIMT) && nn > tc_min;
+    };
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < batch; ++i)
+            if (on_tc(n[i]) == (pass == 1)) p->perm.push_back(i);
+    std::vector<int64_t> tc_n;
+    for (int k = 0; k < batch; ++k) {
+        const int64_t ni = n[p->perm[k]];
+        const bool tc = on_tc(ni);
+        int64_t nb = tc ? 128 : (o.nb > 0 ? o.nb : chol_default_nb(ni, o.precision));
+        if (!tc && nb > ni) nb = ni;  // a matrix smaller than the tile is one tile of its own order
+        const int64_t M = (ni + nb - 1) / nb;
+        p->n.push_back(ni);
         p->nb.push_back(nb);
         p->M.push_back(M);
         store_bytes += al256((size_t)num_tiles(M) * nb * nb * esz);
-        tasks += num_tasks(M) + 1;  // + SOLVE
+        if (tc) tc_n.push_back(ni);
+        else {
+            tasks += num_tasks(M) + 1;  // + SOLVE
+            p->small = k + 1;
+        }
         tiles += num_tiles(M);
         const int nsb = (int)((nb + 31) / 32);
         p->max_nsb2 = nsb * nsb > p->max_nsb2 ? nsb * nsb : p->max_nsb2;
@@ -375,6 +321,18 @@ int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol
             rc = cuda_fail(cudaGetLastError(), "tile list", __FILE__, __LINE__);
             break;
         }
+        if (!tc_n.empty()) {
+            const size_t tcb = oz_batch_bytes((int)tc_n.size(), tc_n.data(), nullptr);
+            if (cudaMalloc(&p->tc_ws, tcb) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("batched plan: device allocation of %zu bytes (tensor-core part) failed", tcb);
+                rc = CHOL_ERR_NOMEM;
+                break;
+            }
+            if ((rc = oz_batch_create(&p->tc, (int)tc_n.size(), tc_n.data(), p->tc_ws, p->h_desc + p->small,
+                                      p->opts)) != CHOL_OK)
+                break;
+        }
         // kernel attributes and the occupancy query are settled before the capture starts
         if ((rc = p->precision == CHOL_FP64 ? set_smem_attr<BatchBody<double>>(df_kernel<BatchBody<double>>)
                                             : set_smem_attr<BatchBody<float>>(df_kernel<BatchBody<float>>)) != CHOL_OK)
@@ -417,21 +375,24 @@ int chol_batch_run(chol_batch_h p, double *const *A, const int64_t *lda, double 
         return CHOL_ERR_HANDLE;
     }
     CHOL_CHECK_ARG(A && lda && B && info, "NULL array argument");
-    for (int i = 0; i < p->batch; ++i) {
-        CHOL_CHECK_ARG(A[i] && B[i] && lda[i] >= p->n[i], "matrix / rhs pointer NULL or lda < n");
-        p->h_desc[i].A = A[i];
-        p->h_desc[i].lda = lda[i];
-        p->h_desc[i].b = B[i];
+    for (int k = 0; k < p->batch; ++k) {
+        const int i = p->perm[k];
+        CHOL_CHECK_ARG(A[i] && B[i] && lda[i] >= p->n[k], "matrix / rhs pointer NULL or lda < n");
+        p->h_desc[k].A = A[i];
+        p->h_desc[k].lda = lda[i];
+        p->h_desc[k].b = B[i];
     }
     CHOL_CUDA(cudaEventRecord(p->t0, p->stream));
     CHOL_CUDA(cudaGraphLaunch(p->exec, p->stream));
     CHOL_CUDA(cudaEventRecord(p->t1, p->stream));
     CHOL_CUDA(cudaStreamSynchronize(p->stream));
-    if (p->h_ctl->status) {
-        set_error("batched: device-side wait expired (site %d)", p->h_ctl->timeout_where);
-        return p->h_ctl->status;
+    for (const Control *c : {(const Control *)p->h_ctl, p->tc ? oz_batch_control(p->tc) : nullptr}) {
+        if (c && c->status) {
+            set_error("batched: device-side wait expired (site %d)", c->timeout_where);
+            return c->status;
+        }
     }
-    memcpy(info, p->h_info, 8 * (size_t)p->batch);
+    for (int k = 0; k < p->batch; ++k) info[p->perm[k]] = p->h_info[k];
     return CHOL_OK;
 }
 
@@ -442,11 +403,12 @@ int chol_batch_stats(chol_batch_h p, chol_stats *st) {
     }
     CHOL_CHECK_ARG(st != nullptr, "stats is NULL");
     memset(st, 0, sizeof(*st));
-    for (int i = 0; i < 4; ++i) st->tasks[i] = (int64_t)p->h_ctl->tasks[i];
+    for (int i = 0; i < 4; ++i)
+        st->tasks[i] = (int64_t)p->h_ctl->tasks[i] + (p->tc ? (int64_t)oz_batch_control(p->tc)->tasks[i] : 0);
     st->nb = p->batch ? p->nb[0] : 0;
     st->schedule = CHOL_SCHED_DATAFLOW;
     st->launches = p->launches;
-    st->trace_records = (int64_t)p->h_ctl->trace_count;
+    st->trace_records = (int64_t)p->h_ctl->trace_count + (p->tc ? (int64_t)oz_batch_control(p->tc)->trace_count : 0);
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p->t0, p->t1) == cudaSuccess) st->device_ms = ms;
     return CHOL_OK;

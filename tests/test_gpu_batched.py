@@ -47,7 +47,7 @@ def test_batched_fp64_matches_solo_and_oracle(cap):
     for k, (A, L, x, b) in enumerate(zip(As, Ls, Xs, Bs)):
         n = A.shape[0]
         assert oracle.backward_error(A, x.reshape(-1, 1), b.reshape(-1, 1)) <= 1e-14
-        if k % 6 == 0 or n <= 33 or n == 2048:
+        if k % 6 == 0 or n <= 33 or n > 1024:
             nb = cap if cap > 0 else chol.chol_default_nb(n, "fp64")
             nb = min(nb, n)
             Ls_solo, info_s, _, rc = _solo(A, nb)
@@ -63,7 +63,11 @@ def test_batched_fp64_matches_solo_and_oracle(cap):
 def _solo(A, nb):
     import paper_2606_11937_gb300 as chol
     from gpu_common import gpu_factor
-    # the batched FP64 bodies are the DFMA ones: compare with that engine
+    # a batch factors matrices of order above 1024 on the tensor-core engine
+    # (tile order 128, the default single factorization), the others with the
+    # DFMA bodies at the batch's tile order
+    if A.shape[0] > 1024:
+        return gpu_factor(A, schedule="dataflow", nb=128)
     return gpu_factor(A, schedule="dataflow", nb=nb, flags=chol.CHOL_FLAG_FP64_SIMT)
 
 
@@ -112,3 +116,72 @@ def test_batched_arguments():
         chol.chol_batch_plan([10, 4096])
     with pytest.raises(chol.CholError):
         chol.chol_batch_plan([10], chol.opts(precision="bf16"))
+
+
+def test_batched_tensor_core_part():
+    """FP64 matrices of order above 1024 run in the batch's tensor-core part
+    (one persistent kernel of the tensor-core engine for all of them, with
+    the fused SOLVE task): each factor equals the single default FP64
+    factorization (tile order 128) bit for bit, every solution reaches the
+    1e-14 backward error, a failing large matrix reports the oracle's info and
+    leaves the others untouched, a batch of large matrices only works, and
+    CHOL_FLAG_FP64_SIMT keeps every matrix on the CUDA-core bodies."""
+    import paper_2606_11937_gb300 as chol
+    ns = [1100, 300, 2048, 1025, 64, 1536, 700, 1300]
+    As, Bs = make_batch(ns, 130)
+    plan = chol.chol_batch_plan(ns)
+    Ls, Xs, info = run_batch(plan, As, Bs)
+    assert info == [0] * len(ns)
+    for A, L, x, b in zip(As, Ls, Xs, Bs):
+        n = A.shape[0]
+        assert oracle.backward_error(A, x.reshape(-1, 1), b.reshape(-1, 1)) <= 1e-14
+        if n > 1024:
+            Lsolo, info_s, _, rc = _solo(A, 128)
+            assert rc == 0 and info_s == 0 and np.array_equal(L, Lsolo), n
+    # a failure inside the tensor-core part
+    bad = [A.copy() for A in As]
+    bad[5][900, 900] = -1e6
+    _, want = oracle.potrf_unblocked(bad[5])
+    L2, X2, info2 = run_batch(plan, bad, Bs)
+    assert info2[5] == want and all(info2[i] == 0 for i in range(len(ns)) if i != 5)
+    for i in range(len(ns)):
+        if i != 5:
+            assert np.array_equal(L2[i], Ls[i]) and np.array_equal(X2[i], Xs[i])
+    plan.close()
+    # only large matrices
+    big = [1200, 1800, 1030]
+    Ab, Bb = make_batch(big, 150)
+    plan = chol.chol_batch_plan(big)
+    Lb, Xb, infob = run_batch(plan, Ab, Bb)
+    assert infob == [0] * 3
+    for A, x, b in zip(Ab, Xb, Bb):
+        assert oracle.backward_error(A, x.reshape(-1, 1), b.reshape(-1, 1)) <= 1e-14
+    plan.close()
+    # forced onto the CUDA-core bodies
+    plan = chol.chol_batch_plan(big, chol.opts(nb=64, flags=chol.CHOL_FLAG_FP64_SIMT))
+    Ls2, Xs2, infos2 = run_batch(plan, Ab, Bb)
+    assert infos2 == [0] * 3
+    from gpu_common import gpu_factor
+    for A, L in zip(Ab, Ls2):
+        Lsolo, _, _, rc = gpu_factor(A, schedule="dataflow", nb=64, flags=chol.CHOL_FLAG_FP64_SIMT)
+        assert rc == 0 and np.array_equal(L, Lsolo)
+    plan.close()
+
+
+def test_batched_tensor_core_split_order():
+    """tc_min_order = 256: the matrices of order above 256 run in the
+    tensor-core part and each equals the single factorization with
+    CHOL_FLAG_FP64_TC at tile order 128 bit for bit."""
+    import paper_2606_11937_gb300 as chol
+    from gpu_common import gpu_factor
+    ns = [200, 257, 640, 1100, 100]
+    As, Bs = make_batch(ns, 170)
+    plan = chol.chol_batch_plan(ns, chol.opts(tc_min_order=256))
+    Ls, Xs, info = run_batch(plan, As, Bs)
+    assert info == [0] * len(ns)
+    for A, L, x, b in zip(As, Ls, Xs, Bs):
+        assert oracle.backward_error(A, x.reshape(-1, 1), b.reshape(-1, 1)) <= 1e-14
+        if A.shape[0] > 256:
+            Lsolo, _, _, rc = gpu_factor(A, schedule="dataflow", nb=128, flags=chol.CHOL_FLAG_FP64_TC)
+            assert rc == 0 and np.array_equal(L, Lsolo), A.shape[0]
+    plan.close()
