@@ -71,12 +71,12 @@ def run_batched(args, world, rank, local):
     tuned = None
     if cap == 0:
         # autotune on this batch, timed on the real plan: the tile-order cap of
-        # the CUDA-core bodies, the engine split (FP64: matrices above order
-        # 1024 on the tensor-core engine, or every matrix on the CUDA cores)
-        # and the priority order of the ready queue
+        # the CUDA-core bodies, the engine split (matrices above a split order
+        # on the tensor-core bodies, or every matrix on the CUDA cores) and
+        # the priority order of the ready queue
         # (engine split: (flags, order above which a matrix goes to the tensor cores))
         engines = ([(0, 64), (0, 128), (0, 256), (0, 512), (0, 1024), (chol.CHOL_FLAG_FP64_SIMT, 0)]
-                   if prec == "fp64" else [(0, 0)])
+                   if prec == "fp64" else [(0, 128), (0, 256), (0, 512), (0, 1024), (0, 2048)])
         trials = []
         for c in (32, 64, 128, 256):
             for e, tmin in engines:
@@ -95,7 +95,7 @@ def run_batched(args, world, rank, local):
     else:
         tc_min = args.tc_min_order
     plan = chol.chol_batch_plan(ns, chol.opts(nb=cap, precision=prec, flags=flags, tc_min_order=tc_min))
-    tc_part = prec == "fp64" and not (flags & chol.CHOL_FLAG_FP64_SIMT) and any(n > (tc_min or 1024) for n in ns)
+    tc_part = (not (prec == "fp64" and flags & chol.CHOL_FLAG_FP64_SIMT)) and any(n > (tc_min or 1024) for n in ns)
     flops = sum(n ** 3 / 3.0 for n in ns)
     solve_flops = sum(2.0 * n * n for n in ns)
 
@@ -131,12 +131,19 @@ def run_batched(args, world, rank, local):
         total_flops = float(t.item())
     value = total_flops / (ms / 1e3) / 1e12
     achieved = flops / (statistics.mean(kms) / 1e3) / 1e12
-    # ceilings: the tensor-core part (most of the flops of an FP64 batch) against
-    # the exact-slicing ceiling (sustained bf16 / 36); CUDA-core bodies against
-    # the FP64 pipe or the FP32 FMA pipe (152 SMs x 128 lanes x 2 flop x 2.07 GHz)
-    if tc_part:
-        bound, peak = "tensor", bench.measured_peaks().get("bf16_tflops_sustained", 1704.0) / 36.0
+    # ceilings: the tensor-core part (most of the flops of the batch) against
+    # the exact-slicing ceiling (FP64: bf16 / 36) or the three-TF32-product
+    # ceiling (FP32: bf16 x 1/2 nominal TF32 ratio / 3), from the measured bf16
+    # burst rate (one graph launch of a fraction of a second); CUDA-core bodies
+    # against the FP64 pipe or the FP32 FMA pipe (152 SMs x 128 lanes x 2 flop
+    # x 2.07 GHz)
+    bf16 = bench.measured_peaks().get("bf16_tflops", 1913.8)
+    if tc_part and prec == "fp64":
+        bound, peak = "tensor", bf16 / 36.0
         kernel = "df_kernel<OzBatchBody> + df_kernel<BatchBody<double>>"
+    elif tc_part:
+        bound, peak = "tensor", bf16 / 2 / 3
+        kernel = "df_kernel<MixedBatchBody> + df_kernel<BatchBody<float>>"
     elif prec == "fp64":
         bound, peak, kernel = "alu", bench.FP64_PEAK_TFLOPS, "df_kernel<BatchBody<double>>"
     else:
@@ -148,7 +155,7 @@ def run_batched(args, world, rank, local):
                 "config": {"workload": f"batched factor+solve of {count} SPD systems, n log-uniform [32, 2048] "
                                        f"(seed 3), A_i = G_i G_i^T/n_i + I, 1 RHS each, {prec}, one graph launch",
                            "batch": count, "tile_cap": cap, "precision": prec, "flags": flags,
-                           "tensor_core_part": f"FP64 matrices of order above {tc_min or 1024}" if tc_part else None,
+                           "tensor_core_part": f"matrices of order above {tc_min or 1024}" if tc_part else None,
                            "sum_n3_over_3": flops, "parallelism": f"contiguous shards x{world}",
                            "l2": "inputs larger than L2"},
                 "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",

@@ -139,9 +139,9 @@ typedef struct {
     void *stream;           /* cudaStream_t; NULL = legacy default stream */
     int32_t num_ctas;       /* dataflow grid size; 0 = default (4 CTAs per SM for the CUDA-core
                                bodies, 1 per SM for the tensor-core body) */
-    int32_t tc_min_order;   /* batched FP64 plans: matrices of order above this run on the tensor-core
-                               engine (0 = 1024, the order above which a single FP64 factorization
-                               uses it by default) */
+    int32_t tc_min_order;   /* batched plans: matrices of order above this run on tensor-core bodies
+                               (0 = 1024, the order above which a single FP64 factorization uses
+                               them by default; 2048 keeps every matrix on the CUDA cores) */
     chol_trace_rec *trace;  /* device buffer of trace_capacity records, or NULL */
     int64_t trace_capacity;
 } chol_opts;
@@ -279,15 +279,19 @@ typedef struct chol_batch_s *chol_batch_h;
  * n[i] (host array, 1 <= n[i] <= 2048, batch <= 65535), 1 right-hand side
  * each, in one persistent kernel launch
  * that is captured once into a CUDA graph and replayed by chol_batch_run.
- * precision: CHOL_FP64 or CHOL_FP32 (true binary32 arithmetic).  The tile
+ * precision: CHOL_FP64 or CHOL_FP32 (binary32 tiles and results).  The tile
  * order of each matrix comes from the autotuner's table for its n (opts->nb
- * > 0 forces one nb for all).  In FP64 plans the matrices of order above 1024
- * (or above opts->tc_min_order) run on the tensor-core engine: tiles of order
- * 128, all of them in one persistent kernel of their own, each with the bits
- * of a single factorization of it with CHOL_FLAG_FP64_TC and nb = 128 (the
- * default single factorization above order 1024); opts->nb applies to the
- * others, and CHOL_FLAG_FP64_SIMT in opts->flags keeps every matrix on the
- * CUDA-core bodies. */
+ * > 0 forces one nb for all).  The matrices of order above 1024 (or above
+ * opts->tc_min_order) run on tensor-core bodies: tiles of order 128, all of
+ * them in one persistent kernel of their own.  In FP64 plans that is the
+ * exact-slice engine, each matrix with the bits of a single factorization of
+ * it with CHOL_FLAG_FP64_TC and nb = 128 (the default single factorization
+ * above order 1024); CHOL_FLAG_FP64_SIMT in opts->flags keeps every matrix on
+ * the CUDA-core bodies.  In FP32 plans it is the mixed-precision engine's FP32
+ * mode (binary64 POTRF, binary32 TRSM, SYRK/GEMM as three TF32 products with
+ * binary32 accumulation), each matrix with the bits of chol_mixed_factor at
+ * CHOL_FP32 and nb = 128, solved in binary32.  The other matrices run in true
+ * binary32 (FP32) or binary64 arithmetic on the CUDA cores with opts->nb. */
 int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol_batch_h *out);
 
 /* Factor every A[i] in place (lower triangle <- L_i) and overwrite B[i] with

@@ -13,7 +13,9 @@
 // order above 1024 (where a single factorization runs on the tensor cores)
 // form a part of their own: tiles of order 128 and one persistent kernel of
 // the tensor-core engine for all of them (batched_tc.cu), before the
-// persistent kernel of the others; internally the smaller matrices come
+// persistent kernel of the others; in FP32 batches the same split puts the
+// larger matrices on the tensor-core bodies of the mixed-precision engine in
+// its FP32 mode (batched_mixed.cu).  Internally the smaller matrices come
 // first (a permutation maps them back to the caller's order).
 #include <string.h>
 
@@ -28,6 +30,10 @@ struct BatchSmem {
     SimtSmem<T> simt;
     T y[2048];          // right-hand side of the SOLVE task (n <= 2048)
 };
+
+static_assert(sizeof(SolveScratch<double>) <= sizeof(SimtSmem<double>) &&
+                  sizeof(SolveScratch<float>) <= sizeof(SimtSmem<float>),
+              "the SOLVE task's scratch fits in the tile bodies' scratch");
 
 template <typename T>
 struct BatchBody {
@@ -56,7 +62,7 @@ struct BatchBody {
         uint64_t t0 = 0;
         if (a.trace && threadIdx.x == 0) t0 = global_ns();
         const MatDesc d = g.desc[m];
-        const bool skip = (a.flags & CHOL_FLAG_NOOP) || ld_acquire_s32(g.failed + m);
+        const bool skip = batch_skip(a, g.failed, m);
         if (!skip) {
             switch (type) {
             case T_POTRF: {
@@ -75,17 +81,17 @@ struct BatchBody {
         if (threadIdx.x == 0) task_done_bookkeeping(a, type, m, I, K, J, t0);
     }
 
-    // L L^T x = b for matrix m, one CTA: column-oriented forward substitution
-    // (y_k = y_k / L_kk, then y_i -= L_ik y_k for i > k) and row-oriented
-    // backward substitution (x_k = (y_k - sum_{i>k} L_ik x_i) / L_kk).
+    // L L^T x = b for matrix m, one CTA: forward and backward substitution
+    // blocked by chunks of 32 rows (tiles_solve).
     static __device__ void solve(const Args &g, const SchedArgs &a, int m, Smem &sm) {
         const MatDesc d = g.desc[m];
         uint64_t t0 = 0;
         if (a.trace && threadIdx.x == 0) t0 = global_ns();
-        const bool skip = (a.flags & CHOL_FLAG_NOOP) || ld_acquire_s32(g.failed + m);
+        const bool skip = batch_skip(a, g.failed, m);
         const int n = d.n, nb = d.nb;
         if (!skip) {
-            tiles_solve<T>(reinterpret_cast<const T *>(d.store), nb, n, d.b, sm.y);
+            tiles_solve<T>(reinterpret_cast<const T *>(d.store), nb, n, d.b, sm.y,
+                           *reinterpret_cast<SolveScratch<T> *>(&sm.simt));
         }
         __syncthreads();
         if (threadIdx.x == 0 && a.trace) {
@@ -114,7 +120,8 @@ struct chol_batch_s {
     std::vector<int64_t> n, nb, M;      // internal order: matrices of the CUDA-core part, then the tensor-core part
     std::vector<int32_t> perm;          // perm[k] = caller's index of internal matrix k
     int32_t small = 0;                  // matrices of the CUDA-core part
-    OzBatchPart *tc = nullptr;          // tensor-core part (matrices small .. batch-1), or null
+    OzBatchPart *tc = nullptr;          // FP64 tensor-core part (matrices small .. batch-1), or null
+    MixedBatchPart *mtc = nullptr;      // FP32 tensor-core part (matrices small .. batch-1), or null
     void *tc_ws = nullptr;
     chol_opts opts{};
     int64_t total_tasks = 0, total_tiles = 0;
@@ -162,6 +169,13 @@ static int record_batch(chol_batch_s *p) {
             return rc;
         launches += l;
     }
+    if (p->mtc) {
+        int l = 0;
+        if ((rc = mixed_batch_record(p->mtc, p->d_desc + p->small, p->d_info + p->small, p->d_failed + p->small, st,
+                                     &l)) != CHOL_OK)
+            return rc;
+        launches += l;
+    }
     if (p->small > 0) {
         typename BatchBody<T>::Args g{p->d_desc, p->d_info, p->d_failed};
         SchedArgs a{p->d_ctl, p->opts.trace, p->opts.trace_capacity, p->opts.flags, 0};
@@ -193,6 +207,7 @@ void chol_batch_free(chol_batch_h p) {
     if (p->graph) cudaGraphDestroy(p->graph);
     if (p->ws) cudaFree(p->ws);
     if (p->tc) oz_batch_destroy(p->tc);
+    if (p->mtc) mixed_batch_destroy(p->mtc);
     if (p->tc_ws) cudaFree(p->tc_ws);
     if (p->h_desc) cudaFreeHost(p->h_desc);
     if (p->h_info) cudaFreeHost(p->h_info);
@@ -227,13 +242,14 @@ int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol
             return CHOL_ERR_ARG;
         }
     }
-    // FP64 matrices above order 1024 (or opts->tc_min_order) go to the
+    // matrices above order 1024 (or opts->tc_min_order) go to the
     // tensor-core part (1024: the choice of a single FP64 factorization with
-    // the default tile order); the others keep the CUDA-core bodies with the
-    // tile order (cap) of opts->nb
+    // the default tile order), unless CHOL_FLAG_FP64_SIMT keeps an FP64 batch
+    // on the CUDA cores; the others keep the CUDA-core bodies with the tile
+    // order (cap) of opts->nb
     const int64_t tc_min = o.tc_min_order > 0 ? o.tc_min_order : kFp64TcMinN;
     auto on_tc = [&](int64_t nn) {
-        return o.precision == CHOL_FP64 && !(o.flags & CHOL_FLAG_FP64_SIMT) && nn > tc_min;
+        return !(o.precision == CHOL_FP64 && (o.flags & CHOL_FLAG_FP64_SIMT)) && nn > tc_min;
     };
     for (int pass = 0; pass < 2; ++pass)
         for (int i = 0; i < batch; ++i)
@@ -322,16 +338,18 @@ int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol
             break;
         }
         if (!tc_n.empty()) {
-            const size_t tcb = oz_batch_bytes((int)tc_n.size(), tc_n.data(), nullptr);
+            const bool fp64 = p->precision == CHOL_FP64;
+            const size_t tcb = fp64 ? oz_batch_bytes((int)tc_n.size(), tc_n.data(), nullptr)
+                                    : mixed_batch_bytes((int)tc_n.size(), tc_n.data(), nullptr);
             if (cudaMalloc(&p->tc_ws, tcb) != cudaSuccess) {
                 cudaGetLastError();
                 set_error("batched plan: device allocation of %zu bytes (tensor-core part) failed", tcb);
                 rc = CHOL_ERR_NOMEM;
                 break;
             }
-            if ((rc = oz_batch_create(&p->tc, (int)tc_n.size(), tc_n.data(), p->tc_ws, p->h_desc + p->small,
-                                      p->opts)) != CHOL_OK)
-                break;
+            rc = fp64 ? oz_batch_create(&p->tc, (int)tc_n.size(), tc_n.data(), p->tc_ws, p->h_desc + p->small, p->opts)
+                      : mixed_batch_create(&p->mtc, (int)tc_n.size(), tc_n.data(), p->tc_ws, p->opts);
+            if (rc != CHOL_OK) break;
         }
         // kernel attributes and the occupancy query are settled before the capture starts
         if ((rc = p->precision == CHOL_FP64 ? set_smem_attr<BatchBody<double>>(df_kernel<BatchBody<double>>)
@@ -386,7 +404,8 @@ int chol_batch_run(chol_batch_h p, double *const *A, const int64_t *lda, double 
     CHOL_CUDA(cudaGraphLaunch(p->exec, p->stream));
     CHOL_CUDA(cudaEventRecord(p->t1, p->stream));
     CHOL_CUDA(cudaStreamSynchronize(p->stream));
-    for (const Control *c : {(const Control *)p->h_ctl, p->tc ? oz_batch_control(p->tc) : nullptr}) {
+    for (const Control *c : {(const Control *)p->h_ctl, p->tc ? oz_batch_control(p->tc) : nullptr,
+                             p->mtc ? mixed_batch_control(p->mtc) : nullptr}) {
         if (c && c->status) {
             set_error("batched: device-side wait expired (site %d)", c->timeout_where);
             return c->status;
@@ -403,12 +422,12 @@ int chol_batch_stats(chol_batch_h p, chol_stats *st) {
     }
     CHOL_CHECK_ARG(st != nullptr, "stats is NULL");
     memset(st, 0, sizeof(*st));
-    for (int i = 0; i < 4; ++i)
-        st->tasks[i] = (int64_t)p->h_ctl->tasks[i] + (p->tc ? (int64_t)oz_batch_control(p->tc)->tasks[i] : 0);
+    const Control *tcc = p->tc ? oz_batch_control(p->tc) : p->mtc ? mixed_batch_control(p->mtc) : nullptr;
+    for (int i = 0; i < 4; ++i) st->tasks[i] = (int64_t)p->h_ctl->tasks[i] + (tcc ? (int64_t)tcc->tasks[i] : 0);
     st->nb = p->batch ? p->nb[0] : 0;
     st->schedule = CHOL_SCHED_DATAFLOW;
     st->launches = p->launches;
-    st->trace_records = (int64_t)p->h_ctl->trace_count + (p->tc ? (int64_t)oz_batch_control(p->tc)->trace_count : 0);
+    st->trace_records = (int64_t)p->h_ctl->trace_count + (tcc ? (int64_t)tcc->trace_count : 0);
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p->t0, p->t1) == cudaSuccess) st->device_ms = ms;
     return CHOL_OK;

@@ -89,10 +89,15 @@ struct OzBatchBody {
         const OzBatchDesc od = g.desc[m];
         double *store = reinterpret_cast<double *>(g.mdesc[m].store);
         auto tile = [&](int i, int k) { return store + (size_t)tile_index(i, k) * kOzNb * kOzNb; };
-        const bool skip = (a.flags & CHOL_FLAG_NOOP) || ld_acquire_s32(g.failed + m);
+        const bool skip = batch_skip(a, g.failed, m);
         const auto take_ahead = [&a]() { df_take_ahead(a); };
         bool ok = true;
-        if (!skip) {
+        if (skip && sm.os.pend) {
+            // a task of a failed matrix that may start with an epilogue
+            // deferred: complete that one first, so that this task completes
+            // on return like any other
+            ok = ozaki_flush(sm, g.timeout_ns, Done{g, a});
+        } else if (!skip) {
             switch (type) {
             case T_POTRF: {
                 const int li = oz_potrf128(tile(J, J), sm);
@@ -152,9 +157,10 @@ struct OzBatchBody {
         uint64_t t0 = 0;
         if (a.trace && threadIdx.x == 0) t0 = global_ns();
         const MatDesc d = g.mdesc[m];
-        const bool skip = (a.flags & CHOL_FLAG_NOOP) || ld_acquire_s32(g.failed + m);
-        if (!skip) tiles_solve<double>(reinterpret_cast<const double *>(d.store), kOzNb, d.n, d.b,
-                                       reinterpret_cast<double *>(sm.B));
+        const bool skip = batch_skip(a, g.failed, m);
+        double *y = reinterpret_cast<double *>(sm.B);
+        if (!skip) tiles_solve<double>(reinterpret_cast<const double *>(d.store), kOzNb, d.n, d.b, y,
+                                       *reinterpret_cast<SolveScratch<double> *>(y + 2048));
         __syncthreads();
         if (threadIdx.x == 0 && a.trace) {
             const unsigned long long slot = atomicAdd(&a.ctl->trace_count, 1ull);
@@ -172,7 +178,8 @@ struct OzBatchBody {
     }
 };
 
-static_assert(2048 * sizeof(double) <= sizeof(OzSmem::B), "the SOLVE task's right-hand side fits in the B region");
+static_assert(2048 * sizeof(double) + sizeof(SolveScratch<double>) <= sizeof(OzSmem::B),
+              "the SOLVE task's right-hand side and scratch fit in the B region");
 
 struct OzBatchPart {
     int count = 0;

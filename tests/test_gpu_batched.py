@@ -138,15 +138,10 @@ def test_batched_tensor_core_part():
         if n > 1024:
             Lsolo, info_s, _, rc = _solo(A, 128)
             assert rc == 0 and info_s == 0 and np.array_equal(L, Lsolo), n
-    # a failure inside the tensor-core part
-    bad = [A.copy() for A in As]
-    bad[5][900, 900] = -1e6
-    _, want = oracle.potrf_unblocked(bad[5])
-    L2, X2, info2 = run_batch(plan, bad, Bs)
-    assert info2[5] == want and all(info2[i] == 0 for i in range(len(ns)) if i != 5)
-    for i in range(len(ns)):
-        if i != 5:
-            assert np.array_equal(L2[i], Ls[i]) and np.array_equal(X2[i], Xs[i])
+    # failures inside the tensor-core part: one at the first diagonal tile
+    # (every later task of that matrix a no-op while the others still run),
+    # one deep inside
+    _check_failures(plan, As, Bs, Ls, Xs, (3, 5))
     plan.close()
     # only large matrices
     big = [1200, 1800, 1030]
@@ -165,6 +160,62 @@ def test_batched_tensor_core_part():
     for A, L in zip(Ab, Ls2):
         Lsolo, _, _, rc = gpu_factor(A, schedule="dataflow", nb=64, flags=chol.CHOL_FLAG_FP64_SIMT)
         assert rc == 0 and np.array_equal(L, Lsolo)
+    plan.close()
+
+
+def _check_failures(plan, As, Bs, Ls, Xs, which):
+    bad = [A.copy() for A in As]
+    bad[which[0]][5, 5] = -1e6
+    bad[which[1]][900, 900] = -1e6
+    want = {i: oracle.potrf_unblocked(bad[i])[1] for i in which}
+    L2, X2, info2 = run_batch(plan, bad, Bs)
+    for i in range(len(As)):
+        if i in which:
+            assert info2[i] == want[i], (i, info2[i], want[i])
+        else:
+            assert info2[i] == 0 and np.array_equal(L2[i], Ls[i]) and np.array_equal(X2[i], Xs[i]), i
+
+
+def test_batched_fp32_tensor_core_part():
+    """FP32 matrices of order above 1024 run in the batch's tensor-core part
+    (the mixed-precision engine's FP32 bodies: binary64 POTRF, binary32 TRSM,
+    SYRK/GEMM as three TF32 products, tile order 128, one persistent kernel
+    with the fused binary32 SOLVE): each factor equals the single
+    mixed-precision FP32 factorization at tile order 128 bit for bit and is
+    within the binary32 tolerance of the oracle, every solution reaches the
+    binary32 backward error, failing matrices report the oracle's info and
+    leave the others untouched, and tc_min_order = 2048 keeps every matrix on
+    the CUDA cores."""
+    import paper_2606_11937_gb300 as chol
+    ns = [1100, 300, 2048, 1025, 64, 1536, 700, 1300]
+    As, Bs = make_batch(ns, 190)
+    plan = chol.chol_batch_plan(ns, chol.opts(precision="fp32"))
+    Ls, Xs, info = run_batch(plan, As, Bs)
+    assert info == [0] * len(ns)
+    assert plan.stats().tasks[3] > 0
+    for A, L, x, b in zip(As, Ls, Xs, Bs):
+        n = A.shape[0]
+        assert oracle.backward_error(A, x.reshape(-1, 1), b.reshape(-1, 1)) <= 1e-6
+        if n > 1024:
+            _, f = chol.chol_mixed_factor(chol.colmajor(A), chol.opts(precision="fp32", nb=128))
+            assert f.info == 0
+            Lm = np.tril(f.factor().cpu().numpy())
+            f.close()
+            assert np.array_equal(L, Lm), n
+        if n <= 1100:
+            Lref, _ = oracle.potrf_unblocked(A)
+            assert scaled_error(L, Lref, A) <= 1e-5
+    _check_failures(plan, As, Bs, Ls, Xs, (0, 5))
+    plan.close()
+    # every matrix on the CUDA cores
+    plan = chol.chol_batch_plan(ns, chol.opts(precision="fp32", tc_min_order=2048))
+    Lc, Xc, infoc = run_batch(plan, As, Bs)
+    assert infoc == [0] * len(ns)
+    for A, L, x, b in zip(As, Lc, Xc, Bs):
+        assert oracle.backward_error(A, x.reshape(-1, 1), b.reshape(-1, 1)) <= 1e-6
+        if A.shape[0] <= 1100:
+            Lref, _ = oracle.potrf_unblocked(A)
+            assert scaled_error(L, Lref, A) <= 1e-5
     plan.close()
 
 
