@@ -1,8 +1,10 @@
 // mixed.cu -- mixed-precision tiled Cholesky with FP64 iterative refinement.
 //
 // The tiles are kept in binary32.  POTRF of each diagonal tile runs in
-// binary64 (the tile is widened, factored, rounded back), TRSM in binary32 on
-// the CUDA cores, and its epilogue writes the tensor-core operand copies of
+// binary64 on its 128 x 128 diagonal blocks (each block widened, factored in
+// shared memory, rounded back; for tile orders above 128 the blocks below
+// and right of it are solved and updated in binary32 in between), TRSM in
+// binary32 on the CUDA cores, and its epilogue writes the tensor-core operand copies of
 // the panel tile: bf16 / fp16 after an exact power-of-two scaling that puts
 // the tile's largest magnitude in [2^14, 2^15), or tf32-rounded values (hi,
 // and lo = tf32(x - hi) for the 3-product FP32 mode).  SYRK and GEMM run on
@@ -367,8 +369,6 @@ static int mixed_factor_impl(int64_t n, const double *A, int64_t lda, const chol
     const size_t b_hi = a256(tiles * tile_elems * (fmt == OP_TF32 ? 4 : 2));
     const size_t b_lo = o.precision == CHOL_FP32 ? a256(tiles * tile_elems * 4) : 0;
     const size_t b_exp = a256(tiles * 4);
-    const int scr_ctas = grid > 1 ? grid : 1;
-    const size_t b_scr = a256((size_t)scr_ctas * tile_elems * 8);
     const size_t b_ctl = a256(sizeof(Control));
     const size_t b_q = sched == CHOL_SCHED_DATAFLOW ? a256((size_t)2 * ntasks * 8) : 0;
     const size_t b_d = sched == CHOL_SCHED_DATAFLOW ? a256((size_t)ntasks * 4) : 0;
@@ -376,7 +376,7 @@ static int mixed_factor_impl(int64_t n, const double *A, int64_t lda, const chol
     float *store = nullptr;
     void *ws = nullptr;
     CHOL_CUDA(cudaMallocAsync((void **)&store, b_store, st));
-    if (cudaMallocAsync(&ws, b_hi + b_lo + b_exp + b_scr + b_ctl + b_q + b_d, st) != cudaSuccess) {
+    if (cudaMallocAsync(&ws, b_hi + b_lo + b_exp + b_ctl + b_q + b_d, st) != cudaSuccess) {
         cudaFreeAsync(store, st);
         set_error("device allocation of the mixed-precision workspace failed");
         return CHOL_ERR_NOMEM;
@@ -388,10 +388,9 @@ static int mixed_factor_impl(int64_t n, const double *A, int64_t lda, const chol
     g.op_hi = p;
     g.op_lo = b_lo ? (float *)(p + b_hi) : nullptr;
     g.exps = (int32_t *)(p + b_hi + b_lo);
-    g.scratch = (double *)(p + b_hi + b_lo + b_exp);
-    Control *ctl = (Control *)(p + b_hi + b_lo + b_exp + b_scr);
-    unsigned long long *queue = (unsigned long long *)(p + b_hi + b_lo + b_exp + b_scr + b_ctl);
-    int32_t *deps = (int32_t *)(p + b_hi + b_lo + b_exp + b_scr + b_ctl + b_q);
+    Control *ctl = (Control *)(p + b_hi + b_lo + b_exp);
+    unsigned long long *queue = (unsigned long long *)(p + b_hi + b_lo + b_exp + b_ctl);
+    int32_t *deps = (int32_t *)(p + b_hi + b_lo + b_exp + b_ctl + b_q);
     g.precision = o.precision;
     g.fmt = fmt;
     g.timeout_ns = (uint64_t)(o.timeout_s * 1e9);

@@ -24,7 +24,6 @@ struct MixedArgs {
     void *op_hi;               // operand stores, same tile indexing as S
     float *op_lo;
     int32_t *exps;             // per-tile scaling exponent (bf16 / fp16)
-    double *scratch;           // one nb x nb binary64 tile per CTA (POTRF)
     int32_t precision;
     int32_t fmt;
     uint64_t timeout_ns;
@@ -134,17 +133,18 @@ __device__ inline void write_operands(const MixedArgs &g, int64_t t, const float
 // reciprocal), then applied to the columns right of it as one rank-16 update
 // by the 256 threads, each holding an 8-row x (up to 7)-column block of
 // accumulators.  The solved tile is stored back and left in shared memory
-// (Bs, padded rows) for the operand copies.  smem: 2 x 128 x 129 floats.
+// (Bs, padded rows) for the operand copies.  B and L have row pitches ldb
+// and ldl (multiples of 4).  smem: 2 x 128 x 129 floats.
 constexpr int kTrsmP = 129;
-__device__ inline void smem_trsm128_f32(float *B, const float *L, float *smem) {
+__device__ inline void smem_trsm128_f32(float *B, const float *L, float *smem, int ldb = 128, int ldl = 128) {
     constexpr int N = 128, P = kTrsmP, W = 16;
     float *Bs = smem, *Ls = smem + N * P;
     __shared__ float rinv[N];
     const int t = threadIdx.x;
     for (int e = t; e < N * N / 4; e += blockDim.x) {
         const int r = (4 * e) / N, c = (4 * e) % N;
-        const float4 b = __ldcg(reinterpret_cast<const float4 *>(B) + e);
-        const float4 l = __ldcg(reinterpret_cast<const float4 *>(L) + e);
+        const float4 b = __ldcg(reinterpret_cast<const float4 *>(B + (size_t)r * ldb + c));
+        const float4 l = __ldcg(reinterpret_cast<const float4 *>(L + (size_t)r * ldl + c));
         Bs[r * P + c] = b.x; Bs[r * P + c + 1] = b.y; Bs[r * P + c + 2] = b.z; Bs[r * P + c + 3] = b.w;
         Ls[r * P + c] = l.x; Ls[r * P + c + 1] = l.y; Ls[r * P + c + 2] = l.z; Ls[r * P + c + 3] = l.w;
     }
@@ -197,7 +197,7 @@ __device__ inline void smem_trsm128_f32(float *B, const float *L, float *smem) {
     }
     for (int e = t; e < N * N / 4; e += blockDim.x) {
         const int r = (4 * e) / N, c = (4 * e) % N;
-        reinterpret_cast<float4 *>(B)[e] =
+        *reinterpret_cast<float4 *>(B + (size_t)r * ldb + c) =
             make_float4(Bs[r * P + c], Bs[r * P + c + 1], Bs[r * P + c + 2], Bs[r * P + c + 3]);
     }
     __syncthreads();
@@ -218,30 +218,50 @@ __device__ bool mixed_task(const MixedArgs &g, const SchedArgs &a, int m, int I,
     if (!(a.flags & CHOL_FLAG_NOOP)) {
         switch (type) {
         case T_POTRF: {
-            if (nb == kPotrfNb) {  // binary64 in shared memory, the stage area
-                const int li = smem_potrf128<float>(tile(J, J), &sm.stages[0][0]);
-                if (li && threadIdx.x == 0) fail((int64_t)J * nb + li);
-                break;
-            }
-            // widen to binary64, factor, round back
-            double *D = g.scratch + (size_t)blockIdx.x * nb * nb;
+            // binary64 POTRF of each 128 x 128 diagonal block in shared memory
+            // (the stage area); for tile orders above 128, blocked over those
+            // blocks: TRSM of the blocks below and the update of the trailing
+            // blocks in binary32, as the tiles of order 128 would see them
             float *T = tile(J, J);
-            const int64_t cnt = (int64_t)nb * nb;
-            for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) D[i] = (double)__ldcg(T + i);
-            __syncthreads();
-            SimtSmem<double> &ss = *reinterpret_cast<SimtSmem<double> *>(sm.stages);
-            const int li = tile_potrf<double>(D, nb, ss);
-            for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) T[i] = (float)D[i];
-            __syncthreads();
-            if (li && threadIdx.x == 0) fail((int64_t)J * nb + li);
+            const int r = nb / kPotrfNb;
+            SimtSmem<float> &ss = *reinterpret_cast<SimtSmem<float> *>(sm.stages);
+            for (int j = 0; j < r; ++j) {
+                float *Tjj = T + (size_t)j * kPotrfNb * nb + j * kPotrfNb;
+                const int li = smem_potrf128<float>(Tjj, &sm.stages[0][0], nb);
+                if (li) {
+                    if (threadIdx.x == 0) fail((int64_t)J * nb + j * kPotrfNb + li);
+                    break;
+                }
+                for (int i = j + 1; i < r; ++i)
+                    smem_trsm128_f32(T + (size_t)i * kPotrfNb * nb + j * kPotrfNb, Tjj,
+                                     reinterpret_cast<float *>(sm.stages), nb, nb);
+                for (int i = j + 1; i < r; ++i)
+                    for (int k = j + 1; k <= i; ++k) {
+                        float *C = T + (size_t)i * kPotrfNb * nb + k * kPotrfNb;
+                        const float *Ai = T + (size_t)i * kPotrfNb * nb + j * kPotrfNb;
+                        const float *Ak = T + (size_t)k * kPotrfNb * nb + j * kPotrfNb;
+                        if (i == k) region_nt_update<float, true>(C, nb, Ai, nb, Ai, nb, kPotrfNb, kPotrfNb, kPotrfNb, ss);
+                        else region_nt_update<float, false>(C, nb, Ai, nb, Ak, nb, kPotrfNb, kPotrfNb, kPotrfNb, ss);
+                    }
+                __syncthreads();
+            }
         } break;
         case T_TRSM: {
+            // B <- B L^{-T} by column blocks of 128: each block solved in
+            // shared memory, then subtracted from the blocks right of it
             float *B = tile(I, J);
-            if (nb == 128) {
-                smem_trsm128_f32(B, tile(J, J), reinterpret_cast<float *>(sm.stages));
-            } else {
-                SimtSmem<float> &ss = *reinterpret_cast<SimtSmem<float> *>(sm.stages);
-                tile_trsm<float>(B, tile(J, J), nb, ss);
+            const float *L = tile(J, J);
+            const int r = nb / 128;
+            SimtSmem<float> &ss = *reinterpret_cast<SimtSmem<float> *>(sm.stages);
+            for (int j = 0; j < r; ++j) {
+                const float *Ljj = L + (size_t)j * 128 * nb + j * 128;
+                for (int i = 0; i < r; ++i)
+                    smem_trsm128_f32(B + (size_t)i * 128 * nb + j * 128, Ljj, reinterpret_cast<float *>(sm.stages),
+                                     nb, nb);
+                for (int c = j + 1; c < r; ++c)
+                    region_nt_update<float, false>(B + c * 128, nb, B + j * 128, nb, L + (size_t)c * 128 * nb + j * 128,
+                                                   nb, nb, 128, 128, ss);
+                __syncthreads();
             }
             write_operands(g, toff + tile_index(I, J), B, reinterpret_cast<float *>(sm.stages));
         } break;

@@ -31,12 +31,13 @@ __device__ __forceinline__ void potrf_panel_sync() { asm volatile("bar.sync 4, 1
 // ascending column order), the division by the pivot being a multiplication
 // by its reciprocal.  The trailing elements are visited through a table of
 // (i, k) in column-major lower order, so the active ones form a contiguous
-// suffix and all threads stay busy.  All threads (at least 256); smem holds
-// kPotrf128SmemBytes (the padded tile and the reciprocals of its diagonal,
-// at kPotrf128RcpOff, stay there for the caller); returns 0 or the 1-based
-// local column whose pivot is not positive (or NaN).  Ends with a barrier.
+// suffix and all threads stay busy.  All threads (at least 256); A has row
+// pitch ld; smem holds kPotrf128SmemBytes (the padded tile and the
+// reciprocals of its diagonal, at kPotrf128RcpOff, stay there for the
+// caller); returns 0 or the 1-based local column whose pivot is not positive
+// (or NaN).  Ends with a barrier.
 template <typename T>
-__device__ int smem_potrf128(T *A, uint8_t *smem) {
+__device__ int smem_potrf128(T *A, uint8_t *smem, int ld = kPotrfNb) {
     constexpr int N = kPotrfNb;
     constexpr int P = N + 1;  // padded row
     double *S = reinterpret_cast<double *>(smem);
@@ -46,7 +47,7 @@ __device__ int smem_potrf128(T *A, uint8_t *smem) {
     constexpr int kTri = N * (N + 1) / 2;
     for (int e = t; e < N * N; e += nt) {
         const int i = e / N, k = e % N;
-        if (k <= i) S[i * P + k] = (double)__ldcg(A + e);
+        if (k <= i) S[i * P + k] = (double)__ldcg(A + (size_t)i * ld + k);
     }
     for (int k = t; k < N; k += nt) {
         const int off = k * N - k * (k - 1) / 2;
@@ -122,7 +123,7 @@ __device__ int smem_potrf128(T *A, uint8_t *smem) {
     }
     for (int e = t; e < N * N; e += nt) {
         const int i = e / N, k = e % N;
-        if (k <= i) A[e] = (T)S[i * P + k];
+        if (k <= i) A[(size_t)i * ld + k] = (T)S[i * P + k];
     }
     __syncthreads();
     return 0;

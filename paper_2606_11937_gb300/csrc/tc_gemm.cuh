@@ -167,7 +167,7 @@ struct TcShared {
     uint32_t pend_u;     // its accumulator use
     float *pend_C;
     float pend_sa, pend_sb;
-    int32_t pend_nb;
+    int32_t pend_nb, pend_ri, pend_ci;  // the tile's order and the sub-tile's position
     uint64_t pend_task, pend_t0;
 };
 
@@ -228,6 +228,11 @@ __device__ __forceinline__ int tc_failed(const TcShared &ts) { return *(volatile
 __device__ __forceinline__ uint32_t tc_buf(uint32_t u, int cols) { return cols <= 256 ? (u & 1) : 0; }
 __device__ __forceinline__ uint32_t tc_phase(uint32_t u, int cols) { return cols <= 256 ? (u >> 1) : u; }
 
+// Sub-tiles of a tile of order nb: 128 rows (one MMA of M = 128) by NN = 256
+// columns for nb >= 256, else 128; 'cols' tensor-memory columns each, so two
+// accumulators fit and alternate.
+__device__ __forceinline__ int tc_sub_cols(int nb) { return nb >= 256 ? 256 : 128; }
+
 // Epilogue of one sub-tile (rows ri*SR.., columns ci*NN..) from accumulator use
 // u, by the 4 epilogue warps: TMEM -> registers -> shared transpose -> C.  A
 // lane holds one row of a 32 x 32 chunk; the chunk goes through a per-warp
@@ -235,7 +240,7 @@ __device__ __forceinline__ uint32_t tc_phase(uint32_t u, int cols) { return cols
 // 32 lanes on 32 consecutive columns (coalesced).  False if a wait expired.
 __device__ inline bool tc_epilogue_sub(TcShared &ts, float *xpose, float *C, int nb, int ri, int ci, float sa,
                                        float sb, uint32_t u, uint64_t deadline) {
-    const int MH = nb >= 256 ? 2 : 1, NN = nb >= 256 ? 256 : 128, SR = MH * 128, cols = MH * NN;
+    const int MH = 1, NN = tc_sub_cols(nb), SR = 128, cols = NN;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int q = warp - 4;  // TMEM lane quadrant of this warp
     float *xp = xpose + q * 32 * 32;
@@ -285,7 +290,8 @@ struct TcNoDone {
 template <class Done>
 __device__ inline bool tc_epilogue_pending(TcShared &ts, float *xpose, uint64_t deadline, const Done &on_done) {
     if (!ts.pend) return true;
-    const bool ok = tc_epilogue_sub(ts, xpose, ts.pend_C, ts.pend_nb, 0, 0, ts.pend_sa, ts.pend_sb, ts.pend_u, deadline);
+    const bool ok = tc_epilogue_sub(ts, xpose, ts.pend_C, ts.pend_nb, ts.pend_ri, ts.pend_ci, ts.pend_sa, ts.pend_sb,
+                                    ts.pend_u, deadline);
     asm volatile("bar.sync 1, 128;" ::: "memory");  // the 4 epilogue warps only
     if (threadIdx.x == 128 && ok) on_done(ts.pend_task, ts.pend_t0);
     return ok;
@@ -313,9 +319,9 @@ __device__ inline bool tc_flush(TcShared &ts, float *xpose, uint64_t timeout_ns,
 // (four 32 x 32 float transpose buffers).  Called by all 256 threads;
 // returns false if a wait expired.  A deferred sub-tile of the previous call
 // is applied first by the epilogue warps (its completion handed to on_done);
-// with defer_last (tile of order 128: one sub-tile) this call's epilogue is
-// left for the next call or tc_flush, tagged with task / t0.  The producer
-// thread calls producer_idle() after its last load.
+// with defer_last the epilogue of this call's last sub-tile is left for the
+// next call or tc_flush, tagged with task / t0.  The producer thread calls
+// producer_idle() after its last load.
 struct TcNoHook {
     __device__ void operator()() const {}
 };
@@ -325,16 +331,17 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
                                       int nb, int aRow0, int bRow0, float sa, float sb, bool lower,
                                       uint64_t timeout_ns, const Done &on_done = Done(), bool defer_last = false,
                                       uint64_t task = 0, uint64_t t0 = 0, const Hook &producer_idle = Hook()) {
-    const int MH = nb >= 256 ? 2 : 1;          // 128-row halves per sub-tile
-    const int NN = nb >= 256 ? 256 : 128;      // MMA N
+    const int MH = 1;                          // 128-row halves per sub-tile
+    const int NN = tc_sub_cols(nb);            // MMA N
     const int SR = MH * 128;                   // sub-tile rows
     const int cols = MH * NN;                  // tensor-memory columns of a sub-tile
     const int nsr = nb / SR, nsc = nb / NN;
     const int kchunks = nb / (g.tf32 ? 32 : 64);
-    // the three products hi.hi, hi.lo, lo.hi of a tile of order 128 read one
-    // K-chunk of A hi, A lo, B hi and B lo from one slot (each box loaded once)
-    const bool fused = g.passes == 3 && MH == 1 && NN == 128;
-    const int boxes = fused ? 4 : MH + NN / 128;
+    // the three products hi.hi, hi.lo, lo.hi read one K-chunk of A hi, A lo,
+    // B hi and B lo from one slot (each box loaded once)
+    const bool fused = g.passes == 3;
+    const int NB = NN / 128;                   // B boxes of one operand
+    const int boxes = fused ? 2 * MH + 2 * NB : MH + NB;
     const uint32_t stage_bytes = (uint32_t)boxes * kBoxBytes;
     const int nst_fit = (kTcStages * kStageBytes) / (int)stage_bytes;
     const uint32_t nst = (uint32_t)(nst_fit < kTcMaxSlots ? nst_fit : kTcMaxSlots);  // ring slots
@@ -348,7 +355,14 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
     for (int ri = 0; ri < nsr; ++ri)
         for (int ci = 0; ci < nsc; ++ci) nsub += skip(ri, ci) ? 0 : 1;
     const uint32_t iters_per_sub = (uint32_t)(npass * kchunks);
-    const bool defer = defer_last && nsub == 1 && cols <= 256;
+    const bool defer = defer_last && cols <= 256;
+    int last_ri = 0, last_ci = 0;  // the last sub-tile (the one deferred)
+    for (int ri = 0; ri < nsr; ++ri)
+        for (int ci = 0; ci < nsc; ++ci)
+            if (!skip(ri, ci)) {
+                last_ri = ri;
+                last_ci = ci;
+            }
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
@@ -368,12 +382,15 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
                         const uint32_t dst = smem_u32(stages + (size_t)s * stage_bytes);
                         const int x = kc * (g.tf32 ? 32 : 64);
                         if (fused) {
-                            // A hi, A lo, B hi, B lo (products 0 and 2 name the A maps, 0 and 1 the B maps)
+                            // A hi, A lo, B hi (NB boxes), B lo (NB boxes); products 0 and 2
+                            // name the A maps, 0 and 1 the B maps
                             const int ar = aRow0 + ri * SR, br = bRow0 + ci * NN;
                             tma_load_2d(dst, g.mapA[0], &ts.full[s], x, ar);
                             tma_load_2d(dst + kBoxBytes, g.mapA[2], &ts.full[s], x, ar);
-                            tma_load_2d(dst + 2 * kBoxBytes, g.mapB[0], &ts.full[s], x, br);
-                            tma_load_2d(dst + 3 * kBoxBytes, g.mapB[1], &ts.full[s], x, br);
+                            for (int q = 0; q < NB; ++q) {
+                                tma_load_2d(dst + (2 + q) * kBoxBytes, g.mapB[0], &ts.full[s], x, br + q * 128);
+                                tma_load_2d(dst + (2 + NB + q) * kBoxBytes, g.mapB[1], &ts.full[s], x, br + q * 128);
+                            }
                             continue;
                         }
                         for (int h = 0; h < MH; ++h)
@@ -409,14 +426,14 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
                         tc_fence_after();
                         const uint32_t base = smem_u32(stages + (size_t)s * stage_bytes);
                         if (fused) {
-                            // hi.hi + hi.lo + lo.hi per K step (tf32, tile order 128)
+                            // hi.hi + hi.lo + lo.hi per K step (tf32)
                             const uint32_t d = ts.tmem_base + tcol;
 #pragma unroll
                             for (int k4 = 0; k4 < 4; ++k4) {
                                 const uint64_t ahi = sdesc_sw128(base + k4 * 32);
                                 const uint64_t alo = sdesc_sw128(base + kBoxBytes + k4 * 32);
                                 const uint64_t bhi = sdesc_sw128(base + 2 * kBoxBytes + k4 * 32);
-                                const uint64_t blo = sdesc_sw128(base + 3 * kBoxBytes + k4 * 32);
+                                const uint64_t blo = sdesc_sw128(base + (2 + NB) * kBoxBytes + k4 * 32);
                                 tc_mma<true>(d, ahi, bhi, g.idesc, first ? 0u : 1u);
                                 tc_mma<true>(d, ahi, blo, g.idesc, 1u);
                                 tc_mma<true>(d, alo, bhi, g.idesc, 1u);
@@ -448,7 +465,8 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
         for (int ri = 0; ri < nsr && ok; ++ri)
             for (int ci = 0; ci < nsc && ok; ++ci) {
                 if (skip(ri, ci)) continue;
-                if (!defer) ok = tc_epilogue_sub(ts, xpose, C, nb, ri, ci, sa, sb, u, deadline);
+                if (!(defer && ri == last_ri && ci == last_ci))
+                    ok = tc_epilogue_sub(ts, xpose, C, nb, ri, ci, sa, sb, u, deadline);
                 ++u;
             }
         if (!ok) *(volatile int32_t *)&ts.fail = 1;
@@ -461,11 +479,13 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
         ts.acc_uses = acc0 + (uint32_t)nsub;
         ts.pend = defer ? 1 : 0;
         if (defer) {
-            ts.pend_u = acc0;
+            ts.pend_u = acc0 + (uint32_t)nsub - 1;
             ts.pend_C = C;
             ts.pend_sa = sa;
             ts.pend_sb = sb;
             ts.pend_nb = nb;
+            ts.pend_ri = last_ri;
+            ts.pend_ci = last_ci;
             ts.pend_task = task;
             ts.pend_t0 = t0;
         }

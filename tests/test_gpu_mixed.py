@@ -49,17 +49,22 @@ def test_mixed_exact_integer_factor(prec, n, nb):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_mixed_factor_error_and_schedules(prec):
+@pytest.mark.parametrize("nb", [128, 256, 512])
+def test_mixed_factor_error_and_schedules(prec, nb):
+    """Tile orders above 128 factor each diagonal tile by 128 x 128 blocks
+    (binary64 POTRF of each, binary32 TRSM and update between them) and solve
+    each panel tile by column blocks of 128: same error bound, and the same
+    bits under every schedule."""
     import paper_2606_11937_gb300 as chol
     n = 2048
     A = matrix("gram", n, 0)
     Lref, _ = oracle_factor("gram", n, 0)
     outs = []
     for sched in ("dataflow", "fork_join", "fork_join_naive", "left_looking", "top_looking"):
-        rc, h, dA = mixed(A, prec, sched, 128)
+        rc, h, dA = mixed(A, prec, sched, nb)
         assert rc == 0 and h.info == 0
         st = chol.chol_mixed_last_stats()
-        assert tuple(st.tasks) == task_counts(16)
+        assert tuple(st.tasks) == task_counts(n // nb)
         L = np.tril(h.factor().cpu().numpy())
         err = scaled_error(L, Lref, A)
         print(f"{prec} {sched}: scaled error vs FP64 oracle {err:.3e}")
@@ -68,6 +73,20 @@ def test_mixed_factor_error_and_schedules(prec):
         h.close()
     for L in outs[1:]:
         assert np.array_equal(outs[0], L)
+
+
+@pytest.mark.parametrize("nb,col", [(128, 300), (256, 400), (256, 100), (512, 1100)])
+def test_mixed_info_inside_blocked_potrf(nb, col):
+    """A non-positive pivot anywhere inside a diagonal tile (first or later
+    128-block) reports the oracle's info."""
+    A = matrix("gram", 1500, 7).copy()
+    A[col, col] = -1e6
+    _, want = oracle.potrf_unblocked(A)
+    assert want == col + 1
+    for prec in ("fp32", "bf16"):
+        rc, h, dA = mixed(A, prec, "dataflow", nb)
+        assert rc == 0 and h.info == want, (prec, nb, h.info, want)
+        h.close()
 
 
 @pytest.mark.parametrize("prec", PRECS)
