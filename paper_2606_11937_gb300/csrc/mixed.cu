@@ -816,7 +816,7 @@ __global__ void __launch_bounds__(256) tc_test_kernel(const __grid_constant__ Tc
         ga.mapA[p] = (three && p == 2) ? &g.map_lo : &g.map_hi;
         ga.mapB[p] = (three && p == 1) ? &g.map_lo : &g.map_hi;
     }
-    ga.idesc = make_idesc((uint32_t)g.fmt, 128, g.nb >= 256 ? 256 : 128);
+    ga.idesc = make_idesc((uint32_t)g.fmt, 128, (uint32_t)tc_sub_cols(g.nb));
     // two updates in a row exercise the barrier phases across tasks
     bool ok = true;
     for (int rep = 0; rep < 2 && ok; ++rep)

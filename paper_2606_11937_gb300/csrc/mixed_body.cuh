@@ -141,12 +141,26 @@ __device__ inline void smem_trsm128_f32(float *B, const float *L, float *smem, i
     float *Bs = smem, *Ls = smem + N * P;
     __shared__ float rinv[N];
     const int t = threadIdx.x;
-    for (int e = t; e < N * N / 4; e += blockDim.x) {
-        const int r = (4 * e) / N, c = (4 * e) % N;
-        const float4 b = __ldcg(reinterpret_cast<const float4 *>(B + (size_t)r * ldb + c));
-        const float4 l = __ldcg(reinterpret_cast<const float4 *>(L + (size_t)r * ldl + c));
-        Bs[r * P + c] = b.x; Bs[r * P + c + 1] = b.y; Bs[r * P + c + 2] = b.z; Bs[r * P + c + 3] = b.w;
-        Ls[r * P + c] = l.x; Ls[r * P + c + 1] = l.y; Ls[r * P + c + 2] = l.z; Ls[r * P + c + 3] = l.w;
+    // four 16-byte loads of each tile in flight per thread before the stores
+    constexpr int U = 4;
+    for (int e0 = t; e0 < N * N / 4; e0 += blockDim.x * U) {
+        float4 b[U], l[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x, r = (4 * e) / N, c = (4 * e) % N;
+            if (e < N * N / 4) {
+                b[u] = __ldcg(reinterpret_cast<const float4 *>(B + (size_t)r * ldb + c));
+                l[u] = __ldcg(reinterpret_cast<const float4 *>(L + (size_t)r * ldl + c));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * blockDim.x, r = (4 * e) / N, c = (4 * e) % N;
+            if (e < N * N / 4) {
+                Bs[r * P + c] = b[u].x; Bs[r * P + c + 1] = b[u].y; Bs[r * P + c + 2] = b[u].z; Bs[r * P + c + 3] = b[u].w;
+                Ls[r * P + c] = l[u].x; Ls[r * P + c + 1] = l[u].y; Ls[r * P + c + 2] = l[u].z; Ls[r * P + c + 3] = l[u].w;
+            }
+        }
     }
     __syncthreads();
     if (t < N) rinv[t] = 1.0f / Ls[t * P + t];
@@ -281,7 +295,7 @@ __device__ bool mixed_task(const MixedArgs &g, const SchedArgs &a, int m, int I,
                 ga.mapA[p] = (three && p == 2) ? &g.map_lo : &g.map_hi;
                 ga.mapB[p] = (three && p == 1) ? &g.map_lo : &g.map_hi;
             }
-            ga.idesc = make_idesc((uint32_t)g.fmt, 128, nb >= 256 ? 256 : 128);
+            ga.idesc = make_idesc((uint32_t)g.fmt, 128, (uint32_t)tc_sub_cols(nb));
             // the producer takes the next task from the queues once its
             // loads are issued, while the tensor cores and the epilogue finish
             const auto take_ahead = [&a]() { df_take_ahead(a); };

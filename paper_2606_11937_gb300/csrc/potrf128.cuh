@@ -45,9 +45,20 @@ __device__ int smem_potrf128(T *A, uint8_t *smem, int ld = kPotrfNb) {
     double *rcp = reinterpret_cast<double *>(smem + kPotrf128RcpOff);
     const int t = threadIdx.x, nt = blockDim.x;
     constexpr int kTri = N * (N + 1) / 2;
-    for (int e = t; e < N * N; e += nt) {
-        const int i = e / N, k = e % N;
-        if (k <= i) S[i * P + k] = (double)__ldcg(A + (size_t)i * ld + k);
+    // eight loads in flight per thread before their shared-memory stores
+    constexpr int U = 8;
+    for (int e0 = t; e0 < N * N; e0 += nt * U) {
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * nt, i = e / N, k = e % N;
+            v[u] = (e < N * N && k <= i) ? __ldcg(A + (size_t)i * ld + k) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * nt, i = e / N, k = e % N;
+            if (e < N * N && k <= i) S[i * P + k] = (double)v[u];
+        }
     }
     for (int k = t; k < N; k += nt) {
         const int off = k * N - k * (k - 1) / 2;

@@ -228,10 +228,10 @@ __device__ __forceinline__ int tc_failed(const TcShared &ts) { return *(volatile
 __device__ __forceinline__ uint32_t tc_buf(uint32_t u, int cols) { return cols <= 256 ? (u & 1) : 0; }
 __device__ __forceinline__ uint32_t tc_phase(uint32_t u, int cols) { return cols <= 256 ? (u >> 1) : u; }
 
-// Sub-tiles of a tile of order nb: 128 rows (one MMA of M = 128) by NN = 256
-// columns for nb >= 256, else 128; 'cols' tensor-memory columns each, so two
-// accumulators fit and alternate.
-__device__ __forceinline__ int tc_sub_cols(int nb) { return nb >= 256 ? 256 : 128; }
+// Sub-tiles of a tile of order nb (a multiple of 128): 128 rows (one MMA of
+// M = 128) by NN = 256 columns when 256 divides nb, else 128; 'cols'
+// tensor-memory columns each, so two accumulators fit and alternate.
+__host__ __device__ __forceinline__ int tc_sub_cols(int nb) { return nb % 256 == 0 ? 256 : 128; }
 
 // Epilogue of one sub-tile (rows ri*SR.., columns ci*NN..) from accumulator use
 // u, by the 4 epilogue warps: TMEM -> registers -> shared transpose -> C.  A

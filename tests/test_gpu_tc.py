@@ -43,7 +43,7 @@ def operands(prec, nb, seed, eA, eB):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32", "fp32"])
-@pytest.mark.parametrize("nb", [128, 256, 512])
+@pytest.mark.parametrize("nb", [128, 256, 384, 512])
 @pytest.mark.parametrize("lower", [False, True])
 def test_tc_tile_update(prec, nb, lower):
     import torch
@@ -65,8 +65,10 @@ def test_tc_tile_update(prec, nb, lower):
         absum += np.abs(a) @ np.abs(b).T * s
     tol = [(2 * nb + 8) * 2.0 ** -24 * absum + 2.0 ** -23 * np.abs(C[r].astype(np.float64)) for r in range(2)]
     mask = np.ones((nb, nb), dtype=bool)
-    if lower and nb >= 512:
-        SR, NN = 256, 256   # sub-tiles strictly above the diagonal are skipped
+    if lower:
+        # sub-tiles (128 rows by 256 columns where 256 divides nb, else 128)
+        # strictly above the diagonal are skipped
+        SR, NN = 128, (256 if nb % 256 == 0 else 128)
         for ri in range(nb // SR):
             for ci in range(nb // NN):
                 if ci * NN >= (ri + 1) * SR:
