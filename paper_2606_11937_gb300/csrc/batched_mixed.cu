@@ -67,7 +67,7 @@ struct MixedBatchBody {
         }
     };
     static __device__ void flush(const Args &g, const SchedArgs &a, Smem &sm) {
-        const bool ok = tc_flush(sm.ts, sm.xpose, g.mx.timeout_ns, Done{g, a});
+        const bool ok = tc_flush(sm.ts, g.mx.timeout_ns, Done{g, a});
         if (!ok && threadIdx.x == 0) fail_timeout(a);
     }
     static __device__ __forceinline__ void cta_init(const Args &, Smem &sm) { tc_cta_init(sm.ts); }
@@ -84,7 +84,7 @@ struct MixedBatchBody {
             // a task of a failed matrix that may start with an epilogue
             // deferred: complete that one first, so that this task completes
             // on return like any other
-            ok = tc_flush(sm.ts, sm.xpose, g.mx.timeout_ns, Done{g, a});
+            ok = tc_flush(sm.ts, g.mx.timeout_ns, Done{g, a});
         } else if (!skip) {
             const auto fail = [&g, m](int64_t col) {
                 g.info[m] = col;

@@ -110,7 +110,7 @@ struct MixedBody {
         }
     };
     static __device__ void flush(const Args &g, const SchedArgs &a, Smem &sm) {
-        const bool ok = tc_flush(sm.ts, sm.xpose, g.timeout_ns, Done{g, a});
+        const bool ok = tc_flush(sm.ts, g.timeout_ns, Done{g, a});
         if (!ok && threadIdx.x == 0) {
             if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 3;
             st_release_s32(&a.ctl->abort, 1);
@@ -820,7 +820,7 @@ __global__ void __launch_bounds__(256) tc_test_kernel(const __grid_constant__ Tc
     // two updates in a row exercise the barrier phases across tasks
     bool ok = true;
     for (int rep = 0; rep < 2 && ok; ++rep)
-        ok = tc_tile_update(sm.ts, &sm.stages[0][0], sm.xpose, ga, g.C + (size_t)rep * g.nb * g.nb, g.nb, 0, g.nb,
+        ok = tc_tile_update(sm.ts, &sm.stages[0][0], ga, g.C + (size_t)rep * g.nb * g.nb, g.nb, 0, g.nb,
                             ldexpf(1.f, -g.eA), ldexpf(1.f, -g.eB), g.lower != 0, 2000000000ull);
     if (threadIdx.x == 0) *g.ok = ok ? 1 : 0;
     tc_cta_fini(sm.ts);

@@ -31,7 +31,6 @@ struct MixedArgs {
 
 struct MixedSmem {
     uint8_t stages[kTcStages][kStageBytes];
-    float xpose[4 * 32 * 32];   // epilogue transpose buffers
     TcShared ts;
 };
 static_assert(sizeof(SimtSmem<double>) <= sizeof(MixedSmem::stages), "SIMT scratch must fit in the stage area");
@@ -299,7 +298,7 @@ __device__ bool mixed_task(const MixedArgs &g, const SchedArgs &a, int m, int I,
             // the producer takes the next task from the queues once its
             // loads are issued, while the tensor cores and the epilogue finish
             const auto take_ahead = [&a]() { df_take_ahead(a); };
-            ok = tc_tile_update(sm.ts, &sm.stages[0][0], sm.xpose, ga, tile(I, K), nb, (int)(ta * nb),
+            ok = tc_tile_update(sm.ts, &sm.stages[0][0], ga, tile(I, K), nb, (int)(ta * nb),
                                 (int)(tb * nb), sa, sb, type == T_SYRK, g.timeout_ns, done, a.dfl != nullptr,
                                 pack_task(m, I, K, J), t0, take_ahead);
         } break;

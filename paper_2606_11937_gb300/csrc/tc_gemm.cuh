@@ -234,46 +234,49 @@ __device__ __forceinline__ uint32_t tc_phase(uint32_t u, int cols) { return cols
 __host__ __device__ __forceinline__ int tc_sub_cols(int nb) { return nb % 256 == 0 ? 256 : 128; }
 
 // Epilogue of one sub-tile (rows ri*SR.., columns ci*NN..) from accumulator use
-// u, by the 4 epilogue warps: TMEM -> registers -> shared transpose -> C.  A
-// lane holds one row of a 32 x 32 chunk; the chunk goes through a per-warp
-// shared-memory transpose so that C is read and written row by row with the
-// 32 lanes on 32 consecutive columns (coalesced).  False if a wait expired.
-__device__ inline bool tc_epilogue_sub(TcShared &ts, float *xpose, float *C, int nb, int ri, int ci, float sa,
-                                       float sb, uint32_t u, uint64_t deadline) {
-    const int MH = 1, NN = tc_sub_cols(nb), SR = 128, cols = NN;
+// u, by the 4 epilogue warps: TMEM -> registers -> C.  A lane holds one row of
+// a 32 x 32 chunk (the tensor-memory lane layout) and reads and writes that
+// row's 32 consecutive entries of C with four 32-byte accesses, each warp
+// access touching 32 whole sectors.  False if a wait expired.
+__device__ __forceinline__ void ld_global_v8(const float *p, float *v) {
+    asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+                 : "l"(p));
+}
+__device__ __forceinline__ void st_global_v8(float *p, const float *v) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
+}
+
+__device__ inline bool tc_epilogue_sub(TcShared &ts, float *C, int nb, int ri, int ci, float sa, float sb, uint32_t u,
+                                       uint64_t deadline) {
+    const int NN = tc_sub_cols(nb), SR = 128, cols = NN;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int q = warp - 4;  // TMEM lane quadrant of this warp
-    float *xp = xpose + q * 32 * 32;
     const uint32_t b = tc_buf(u, cols), k = tc_phase(u, cols);
-    for (int h = 0; h < MH; ++h) {  // pull this warp's rows of the sub-tile into L2
-        const float *rp = C + (size_t)(ri * SR + h * 128 + q * 32 + lane) * nb + ci * NN;
-        for (int l = 0; l < NN; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + l));
-    }
+    // this lane's row of the sub-tile: 32-byte aligned (nb a multiple of 128)
+    float *cr = C + (size_t)(ri * SR + q * 32 + lane) * nb + ci * NN;
+    for (int l = 0; l < NN; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(cr + l));  // into L2
     bool got = true;
     if (lane == 0) got = mbar_wait(&ts.acc_full[b], k & 1, deadline);
     got = __shfl_sync(0xffffffffu, got, 0);
     if (!got) return false;
     tc_fence_after();
     const uint32_t tcol = b * (uint32_t)cols;
-    for (int h = 0; h < MH; ++h) {
-        const int row0 = ri * SR + h * 128 + q * 32;
-        for (int c = 0; c < NN; c += 32) {
-            // the 32 rows of C this chunk updates are requested first, so their
-            // L2 latency overlaps the tensor-memory load and the transpose
-            float *cb = C + (size_t)row0 * nb + ci * NN + c + lane;
-            float cv[32];
+    for (int c = 0; c < NN; c += 32) {
+        // the row's 32 entries of C are requested first, so their latency
+        // overlaps the tensor-memory load
+        float cv[32];
 #pragma unroll
-            for (int rr = 0; rr < 32; ++rr) cv[rr] = __ldcg(cb + (size_t)rr * nb);
-            uint32_t r[32];
-            tmem_ld32(ts.tmem_base + ((uint32_t)(q * 32) << 16) + tcol + (uint32_t)(h * NN + c), r);
-            tmem_ld_wait();
+        for (int v = 0; v < 4; ++v) ld_global_v8(cr + c + 8 * v, cv + 8 * v);
+        uint32_t r[32];
+        tmem_ld32(ts.tmem_base + ((uint32_t)(q * 32) << 16) + tcol + (uint32_t)c, r);
+        tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) xp[j * 32 + (lane ^ j)] = (__uint_as_float(r[j]) * sa) * sb;
-            __syncwarp();
+        for (int j = 0; j < 32; ++j) cv[j] -= (__uint_as_float(r[j]) * sa) * sb;
 #pragma unroll
-            for (int rr = 0; rr < 32; ++rr) cb[(size_t)rr * nb] = cv[rr] - xp[lane * 32 + (rr ^ lane)];
-            __syncwarp();
-        }
+        for (int v = 0; v < 4; ++v) st_global_v8(cr + c + 8 * v, cv + 8 * v);
     }
     tc_fence_before();
     __syncwarp();
@@ -288,10 +291,10 @@ struct TcNoDone {
 // The epilogue warps apply a deferred sub-tile, if any, then one thread hands
 // its word to on_done (after all 4 warps' stores: the named barrier).
 template <class Done>
-__device__ inline bool tc_epilogue_pending(TcShared &ts, float *xpose, uint64_t deadline, const Done &on_done) {
+__device__ inline bool tc_epilogue_pending(TcShared &ts, uint64_t deadline, const Done &on_done) {
     if (!ts.pend) return true;
-    const bool ok = tc_epilogue_sub(ts, xpose, ts.pend_C, ts.pend_nb, ts.pend_ri, ts.pend_ci, ts.pend_sa, ts.pend_sb,
-                                    ts.pend_u, deadline);
+    const bool ok =
+        tc_epilogue_sub(ts, ts.pend_C, ts.pend_nb, ts.pend_ri, ts.pend_ci, ts.pend_sa, ts.pend_sb, ts.pend_u, deadline);
     asm volatile("bar.sync 1, 128;" ::: "memory");  // the 4 epilogue warps only
     if (threadIdx.x == 128 && ok) on_done(ts.pend_task, ts.pend_t0);
     return ok;
@@ -300,9 +303,9 @@ __device__ inline bool tc_epilogue_pending(TcShared &ts, float *xpose, uint64_t 
 // Apply a deferred sub-tile now (all threads; ends with a barrier).  False if
 // a wait expired.
 template <class Done>
-__device__ inline bool tc_flush(TcShared &ts, float *xpose, uint64_t timeout_ns, const Done &on_done) {
+__device__ inline bool tc_flush(TcShared &ts, uint64_t timeout_ns, const Done &on_done) {
     bool ok = true;
-    if (threadIdx.x >= 128) ok = tc_epilogue_pending(ts, xpose, global_ns() + timeout_ns, on_done);
+    if (threadIdx.x >= 128) ok = tc_epilogue_pending(ts, global_ns() + timeout_ns, on_done);
     if (!ok) *(volatile int32_t *)&ts.fail = 1;
     __syncthreads();
     ok = !tc_failed(ts);
@@ -315,8 +318,7 @@ __device__ inline bool tc_flush(TcShared &ts, float *xpose, uint64_t timeout_ns,
 // C[nb x nb] -= sa * sb * sum_p A_p B_p^T (sa, sb powers of two, applied one
 // after the other so their product never underflows on its own), A rows
 // starting at row aRow0 of the operand maps, B rows at bRow0.  lower: skip
-// sub-tiles strictly above the diagonal (SYRK).  xpose: 16 KB of shared memory
-// (four 32 x 32 float transpose buffers).  Called by all 256 threads;
+// sub-tiles strictly above the diagonal (SYRK).  Called by all 256 threads;
 // returns false if a wait expired.  A deferred sub-tile of the previous call
 // is applied first by the epilogue warps (its completion handed to on_done);
 // with defer_last the epilogue of this call's last sub-tile is left for the
@@ -327,7 +329,7 @@ struct TcNoHook {
 };
 
 template <class Done = TcNoDone, class Hook = TcNoHook>
-__device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpose, const TcGemmArgs &g, float *C,
+__device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, const TcGemmArgs &g, float *C,
                                       int nb, int aRow0, int bRow0, float sa, float sb, bool lower,
                                       uint64_t timeout_ns, const Done &on_done = Done(), bool defer_last = false,
                                       uint64_t task = 0, uint64_t t0 = 0, const Hook &producer_idle = Hook()) {
@@ -460,13 +462,13 @@ __device__ inline bool tc_tile_update(TcShared &ts, uint8_t *stages, float *xpos
             }
     } else if (warp >= 4) {
         // ---------------- epilogue (a deferred sub-tile of the previous call first)
-        bool ok = tc_epilogue_pending(ts, xpose, deadline, on_done);
+        bool ok = tc_epilogue_pending(ts, deadline, on_done);
         uint32_t u = acc0;
         for (int ri = 0; ri < nsr && ok; ++ri)
             for (int ci = 0; ci < nsc && ok; ++ci) {
                 if (skip(ri, ci)) continue;
                 if (!(defer && ri == last_ri && ci == last_ci))
-                    ok = tc_epilogue_sub(ts, xpose, C, nb, ri, ci, sa, sb, u, deadline);
+                    ok = tc_epilogue_sub(ts, C, nb, ri, ci, sa, sb, u, deadline);
                 ++u;
             }
         if (!ok) *(volatile int32_t *)&ts.fail = 1;
