@@ -81,6 +81,20 @@ int64_t tasks_of(int64_t M) { return M * (M + 1) * (M + 2) / 6; }
 bool fp64_on_tensor_cores(int64_t n) { return chol::fp64_uses_tc(n, 0, 0); }
 int64_t fp64_nb(int64_t n) { return fp64_on_tensor_cores(n) ? 128 : chol_default_nb(n, CHOL_FP64); }
 
+// Persistent grid of a served factorization: the device's SMs shared among
+// the slots (a served factorization of order <= 8192 is bound by its chain of
+// diagonal-tile tasks more than by its updates, so the slots' chains overlap
+// instead of each kernel holding every SM), and no more CTAs than tiles in
+// the lower triangle (the widest a step of the task graph gets).  The bits do
+// not depend on the grid (every tile receives its updates in the same order).
+int served_grid(int64_t n, int64_t nb, int sms, int slots) {
+    const int64_t M = (n + nb - 1) / nb, tiles = M * (M + 1) / 2;
+    int64_t g = sms / (slots > 0 ? slots : 1);
+    if (g < 8) g = 8;
+    if (tiles < g) g = tiles < 4 ? 4 : tiles;
+    return (int)g;
+}
+
 // upper bound of the device bytes a request needs while it runs
 size_t need_bytes(const chol_request &r, bool reuse) {
     const int64_t n = r.n, nrhs = r.nrhs;
@@ -99,8 +113,7 @@ size_t need_bytes(const chol_request &r, bool reuse) {
     const int64_t nb = chol_default_nb(n, r.precision), M = (n + nb - 1) / nb;
     const size_t tiles = (size_t)M * (M + 1) / 2, te = (size_t)nb * nb;
     const size_t per = r.precision == CHOL_FP32 ? 12 : (r.precision == CHOL_TF32 ? 8 : 6);
-    return tiles * te * per + 160 * te * 8 + (size_t)tasks_of(M) * 20 + ir + 4096 +
-           chol::mixed_residual_keep_bytes(n);
+    return tiles * te * per + (size_t)tasks_of(M) * 20 + ir + 4096 + chol::mixed_residual_keep_bytes(n);
 }
 
 size_t keep_bytes_of(const chol_request &r) {
@@ -127,6 +140,7 @@ struct chol_server_s {
     bool stop = false;
     uint64_t next_ticket = 1, use_clock = 0;
     int device = 0;
+    int sms = 152;  // the device's SM count
     // statistics
     std::vector<double> lat_ms;
     int64_t completed = 0, failed = 0, rejected = 0;
@@ -239,6 +253,8 @@ struct chol_server_s {
         o.precision = q.precision;
         o.nb = 0;
         o.schedule = CHOL_SCHED_DATAFLOW;
+        o.num_ctas = served_grid(q.n, q.precision == CHOL_FP64 ? fp64_nb(q.n) : chol_default_nb(q.n, q.precision),
+                                 sms, nslots);
         int rc = CHOL_OK;
         r->res.berr = -1.0;
         r->res.reused_factor = r->reuse ? 1 : 0;
@@ -369,6 +385,7 @@ int chol_server_create(size_t mem_budget_bytes, int32_t slots, const chol_opts *
     if (s->opts.max_iter <= 0) s->opts.max_iter = 30;
     if (!(s->opts.timeout_s > 0)) s->opts.timeout_s = 60.0;
     cudaGetDevice(&s->device);
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     s->slot_req.assign(s->nslots, nullptr);
     for (int i = 0; i < s->nslots; ++i) {
         cudaStream_t st;
