@@ -189,28 +189,54 @@ __global__ void __launch_bounds__(256) residual_kernel(const double *A, int64_t 
 }
 
 // ||A||_inf of the symmetric matrix: row sums of |A|, one thread per row.
+// rows[i] = sum_j |A(i, j)| of the symmetric A given by its lower triangle
+// (column-major, lda): the lower part of row i (j <= i) by thread i, the loads
+// of a warp on consecutive rows of one column, then the part right of the
+// diagonal, which is column i below it, by one warp per column (lanes on
+// consecutive rows) in the second kernel.
 __global__ void anorm_rows_kernel(const double *A, int64_t lda, int64_t n, double *rows) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s = 0.0;
-    for (int64_t j = 0; j <= i; ++j) s += fabs(A[j * lda + i]);      // lower part of row i
-    for (int64_t j = i + 1; j < n; ++j) s += fabs(A[i * lda + j]);  // column i below the diagonal
+    for (int64_t j = 0; j <= i; ++j) s += fabs(A[j * lda + i]);  // lower part of row i
     rows[i] = s;
 }
+__global__ void anorm_cols_kernel(const double *A, int64_t lda, int64_t n, double *rows) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int64_t j = i + 1 + lane; j < n; j += 32) s += fabs(A[i * lda + j]);  // column i below the diagonal
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) rows[i] += s;
+}
 
-// per column: max |R|, max |X|, max |B| (non-negative doubles order like their bits)
-__global__ void colmax_kernel(const double *R, int64_t ldr, const double *X, int64_t ldx, const double *B,
-                              int64_t ldb, int64_t n, int64_t nrhs, unsigned long long *out) {
+// Column maxima of |R|, |X|, |B| (non-negative doubles, so their bit patterns
+// order like the values): reduced over the warp, then the block (256
+// threads), then one atomic per block and quantity.
+__global__ void __launch_bounds__(256) colmax_kernel(const double *R, int64_t ldr, const double *X, int64_t ldx,
+                                                     const double *B, int64_t ldb, int64_t n, int64_t nrhs,
+                                                     unsigned long long *out) {
+    __shared__ double red[3][8];
     const int64_t c = blockIdx.y;
-    double mr = 0, mx = 0, mb = 0;
+    double m[3] = {0, 0, 0};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        mr = fmax(mr, fabs(R[c * ldr + i]));
-        mx = fmax(mx, fabs(X[c * ldx + i]));
-        mb = fmax(mb, fabs(B[c * ldb + i]));
+        m[0] = fmax(m[0], fabs(R[c * ldr + i]));
+        m[1] = fmax(m[1], fabs(X[c * ldx + i]));
+        m[2] = fmax(m[2], fabs(B[c * ldb + i]));
     }
-    atomicMax(out + 3 * c + 0, (unsigned long long)__double_as_longlong(mr));
-    atomicMax(out + 3 * c + 1, (unsigned long long)__double_as_longlong(mx));
-    atomicMax(out + 3 * c + 2, (unsigned long long)__double_as_longlong(mb));
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        for (int o = 16; o > 0; o >>= 1) m[q] = fmax(m[q], __shfl_xor_sync(0xffffffffu, m[q], o));
+        if (lane == 0) red[q][warp] = m[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) v = fmax(v, red[threadIdx.x][w]);
+        atomicMax(out + 3 * c + threadIdx.x, (unsigned long long)__double_as_longlong(v));
+    }
 }
 
 __global__ void to_f32_kernel(const double *R, int64_t ldr, float *D, int64_t n, int64_t nrhs) {
@@ -225,11 +251,18 @@ __global__ void axpy_kernel(double *X, int64_t ldx, const float *D, int64_t n, i
         X[c * ldx + i] += (double)D[c * n + i];
 }
 
-__global__ void max_kernel(const double *v, int64_t n, unsigned long long *out) {
+__global__ void __launch_bounds__(256) max_kernel(const double *v, int64_t n, unsigned long long *out) {
+    __shared__ double red[8];
     double m = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         m = fmax(m, v[i]);
-    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x / 32); ++w) m = fmax(m, red[w]);
+        atomicMax(out, (unsigned long long)__double_as_longlong(m));
+    }
 }
 
 // ------------------------------------------------------------------ GMRES-based refinement helpers
@@ -700,6 +733,7 @@ int chol_mixed_solve(chol_factor_h h, int64_t nrhs, const double *B, int64_t ldb
     do {
         if (h->anorm < 0) {
             anorm_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h->A, h->lda, n, rows);
+            anorm_cols_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(h->A, h->lda, n, rows);
             if (cudaMemsetAsync(mx + 3 * nrhs, 0, 8, st) != cudaSuccess) { rc = CHOL_ERR_CUDA; break; }
             max_kernel<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(rows, n, mx + 3 * nrhs);
             unsigned long long v = 0;
