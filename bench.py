@@ -292,13 +292,14 @@ def run_fp64(args, world, rank, local):
         peak = bf16 / 36.0
         # DRAM bytes (read + write) of the dataflow kernel per task, measured
         # by ncu on a small case of the same configuration (n = 12288, nb = 128,
-        # dataflow + priority: 26.43 GB read + 20.16 GB written over 152 096
-        # tasks = 306.3 KB per task), scaled by this launch's task count.  Per-task
-        # DRAM bytes grow with n as block columns outgrow L2 (251 KB at n = 8192,
-        # 306 KB at 12288, 545 KB measured at 32768), so this is a lower bound.
+        # dataflow + priority: 24.70 GB read + 19.98 GB written over 152 096
+        # tasks = 293.7 KB per task), scaled by this launch's task count.  Per-task
+        # DRAM bytes grow with n as block columns outgrow L2 (250 KB at n = 8192,
+        # 294 KB at 12288, 545 KB measured at 32768 with an earlier kernel), so
+        # this is a lower bound.
         same_cfg = nb == 128 and args.schedule == "dataflow" and args.flags == 18 and args.num_ctas == 0
         m = -(-n // nb)
-        traffic = 306.3e3 * (m * (m + 1) * (m + 2) // 6) if same_cfg else None
+        traffic = 293.7e3 * (m * (m + 1) * (m + 2) // 6) if same_cfg else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_source": "ncu DRAM bytes per task at n=12288 scaled by the task count "
                                                       "(lower bound)" if traffic else None,
