@@ -84,7 +84,8 @@ __device__ __forceinline__ void solve_load(const T *p, T (&v)[V]) {
     }
 }
 
-// L L^T x = b with L in a tile store (row-major tiles of order nb, tile
+// L L^T x = b (the use of the factor the paper motivates in Section 1) with
+// L in a tile store (row-major tiles of order nb, tile
 // (I, K) at index I (I + 1) / 2 + K), one CTA, blocked by chunks of 32 rows.
 // Forward, chunk by chunk: y_c -= L(c, 0:c0) y(0:c0) (one warp per row, its
 // lanes along the row in V-element loads, a warp sum), then y_c = L_cc^{-1}

@@ -1,5 +1,6 @@
 // batched_mixed.cu -- the tensor-core part of a binary32 batched factor +
-// solve plan: every matrix of order above the split order is factored on
+// solve plan (many independent factorizations of Section 3.1 in one
+// dataflow launch of Section 3.2): every matrix of order above the split order is factored on
 // tiles of order 128 with the task bodies of the mixed-precision engine in
 // its FP32 mode (POTRF of a diagonal tile in binary64, TRSM in binary32,
 // SYRK/GEMM as three TF32 products with binary32 accumulation in tensor

@@ -2,8 +2,9 @@
 // shared by the single-matrix engine (mixed.cu) and the tensor-core part of
 // binary32 batches (batched_mixed.cu): the arguments and shared memory of a
 // CTA, the operand copies of a panel tile, the binary32 TRSM of a tile of
-// order 128 and one task (POTRF in binary64, TRSM in binary32, SYRK/GEMM on
-// tcgen05 with binary32 accumulation in tensor memory).
+// order 128 and one task of the tiled right-looking algorithm (Section 3.1,
+// Fig. 1: POTRF in binary64, TRSM in binary32, SYRK/GEMM on tcgen05 with
+// binary32 accumulation in tensor memory).
 #pragma once
 
 #include <cuda.h>
