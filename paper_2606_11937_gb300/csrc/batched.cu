@@ -157,7 +157,7 @@ static int record_batch(chol_batch_s *p) {
     CHOL_CUDA(cudaMemsetAsync(p->d_ctl, 0, sizeof(Control), st));
     CHOL_CUDA(cudaMemsetAsync(p->d_info, 0, sizeof(int64_t) * p->batch, st));
     CHOL_CUDA(cudaMemsetAsync(p->d_failed, 0, sizeof(int32_t) * p->batch, st));
-    const dim3 rgrid((unsigned)p->total_tiles, (unsigned)p->max_nsb2);
+    const dim3 rgrid((unsigned)p->total_tiles, (unsigned)((p->max_nsb2 + kSubPer - 1) / kSubPer));
     batch_repack_kernel<T><<<rgrid, dim3(32, 8), 0, st>>>(p->d_desc, p->d_list);
     CHOL_CUDA(cudaGetLastError());
     int launches = 0, rc = CHOL_OK;

@@ -196,55 +196,94 @@ __device__ void tiles_solve(const T *store, int nb, int n, double *b, T *y, Solv
     else tiles_solve_v<T, 1>(store, nb, n, b, y, s);
 }
 
-// Repack / unpack over a flat list of (matrix, tile); grid.y = 32 x 32 sub-block.
+// Repack / unpack over a flat list of (matrix, tile): a CTA (32 x 8 threads)
+// moves kSubPer consecutive 32 x 32 sub-blocks of one tile (grid.y = groups of
+// kSubPer sub-blocks), all its loads issued before the shared-memory
+// transposes (16 per thread), so that enough bytes are in flight per SM.
+constexpr int kSubPer = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) batch_repack_kernel(const MatDesc *desc, const TileRef *list) {
-    __shared__ T buf[32][33];
+    __shared__ T buf[kSubPer][32][33];
     const TileRef tr = list[blockIdx.x];
     const MatDesc d = desc[tr.m];
-    const int nb = d.nb, nsb = (nb + 31) / 32;
-    if ((int)blockIdx.y >= nsb * nsb) return;
+    const int nb = d.nb, nsb = (nb + 31) / 32, sb0 = blockIdx.y * kSubPer;
+    if (sb0 >= nsb * nsb) return;
     int I, K;
     tile_of(tr.t, I, K);
-    const int sr = blockIdx.y / nsb, sc = blockIdx.y % nsb;
     T *tile = reinterpret_cast<T *>(d.store) + (size_t)tr.t * nb * nb;
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
-        const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
-        T v = T(0);
-        if (r < nb && c < nb) {
-            if (i < d.n && j < d.n) v = j <= i ? (T)d.A[j * d.lda + i] : T(0);
-            else v = i == j ? T(1) : T(0);
+    T v[kSubPer][4];
+#pragma unroll
+    for (int s = 0; s < kSubPer; ++s) {
+        const int sb = sb0 + s, sr = sb / nsb, sc = sb % nsb;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int yy = threadIdx.y + 8 * q;
+            const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
+            const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
+            T x = T(0);
+            if (sb < nsb * nsb && r < nb && c < nb) {
+                if (i < d.n && j < d.n) x = j <= i ? (T)d.A[j * d.lda + i] : T(0);
+                else x = i == j ? T(1) : T(0);
+            }
+            v[s][q] = x;
         }
-        buf[yy][threadIdx.x] = v;
     }
+#pragma unroll
+    for (int s = 0; s < kSubPer; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) buf[s][threadIdx.y + 8 * q][threadIdx.x] = v[s][q];
     __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
-        if (r < nb && c < nb) tile[(size_t)r * nb + c] = buf[threadIdx.x][yy];
+#pragma unroll
+    for (int s = 0; s < kSubPer; ++s) {
+        const int sb = sb0 + s, sr = sb / nsb, sc = sb % nsb;
+        if (sb >= nsb * nsb) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int yy = threadIdx.y + 8 * q;
+            const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
+            if (r < nb && c < nb) tile[(size_t)r * nb + c] = buf[s][threadIdx.x][yy];
+        }
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) batch_unpack_kernel(const MatDesc *desc, const TileRef *list) {
-    __shared__ T buf[32][33];
+    __shared__ T buf[kSubPer][32][33];
     const TileRef tr = list[blockIdx.x];
     const MatDesc d = desc[tr.m];
-    const int nb = d.nb, nsb = (nb + 31) / 32;
-    if ((int)blockIdx.y >= nsb * nsb) return;
+    const int nb = d.nb, nsb = (nb + 31) / 32, sb0 = blockIdx.y * kSubPer;
+    if (sb0 >= nsb * nsb) return;
     int I, K;
     tile_of(tr.t, I, K);
-    const int sr = blockIdx.y / nsb, sc = blockIdx.y % nsb;
     const T *tile = reinterpret_cast<const T *>(d.store) + (size_t)tr.t * nb * nb;
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
-        buf[yy][threadIdx.x] = (r < nb && c < nb) ? tile[(size_t)r * nb + c] : T(0);
+    T v[kSubPer][4];
+#pragma unroll
+    for (int s = 0; s < kSubPer; ++s) {
+        const int sb = sb0 + s, sr = sb / nsb, sc = sb % nsb;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int yy = threadIdx.y + 8 * q;
+            const int r = sr * 32 + yy, c = sc * 32 + threadIdx.x;
+            v[s][q] = (sb < nsb * nsb && r < nb && c < nb) ? tile[(size_t)r * nb + c] : T(0);
+        }
     }
+#pragma unroll
+    for (int s = 0; s < kSubPer; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) buf[s][threadIdx.y + 8 * q][threadIdx.x] = v[s][q];
     __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += 8) {
-        const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
-        const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
-        if (r < nb && c < nb && i < d.n && j < d.n && j <= i) d.A[j * d.lda + i] = (double)buf[threadIdx.x][yy];
+#pragma unroll
+    for (int s = 0; s < kSubPer; ++s) {
+        const int sb = sb0 + s, sr = sb / nsb, sc = sb % nsb;
+        if (sb >= nsb * nsb) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int yy = threadIdx.y + 8 * q;
+            const int r = sr * 32 + threadIdx.x, c = sc * 32 + yy;
+            const int64_t i = (int64_t)I * nb + r, j = (int64_t)K * nb + c;
+            if (r < nb && c < nb && i < d.n && j < d.n && j <= i) d.A[j * d.lda + i] = (double)buf[s][threadIdx.x][yy];
+        }
     }
 }
 
