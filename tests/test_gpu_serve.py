@@ -21,6 +21,9 @@ def _req(server, A, B, fid=0, prec="fp64", reuse=False):
 
 
 def test_served_results_same_alone_and_in_mix():
+    """Alone (one slot: each factorization's persistent grid is the whole
+    device) and in the mix (four slots: a quarter of the SMs each, requests
+    overlapping): the same bits, and the oracle's backward error."""
     import torch
 
     import paper_2606_11937_gb300 as chol
