@@ -219,6 +219,30 @@ def test_batched_fp32_tensor_core_part():
     plan.close()
 
 
+def test_batched_fp32_tensor_core_small_orders():
+    """tc_min_order = 100 in an FP32 plan: matrices of one padded tile of order
+    128 (n = 101, 128), of two tiles with a one-row ragged tile (129) and a few
+    tiles run in the tensor-core part; each equals the single mixed-precision
+    FP32 factorization at tile order 128 bit for bit and reaches the binary32
+    backward error; the matrix below the split stays on the CUDA cores."""
+    import paper_2606_11937_gb300 as chol
+    ns = [101, 128, 129, 250, 90, 384]
+    As, Bs = make_batch(ns, 210)
+    plan = chol.chol_batch_plan(ns, chol.opts(precision="fp32", tc_min_order=100))
+    Ls, Xs, info = run_batch(plan, As, Bs)
+    assert info == [0] * len(ns)
+    for A, L, x, b in zip(As, Ls, Xs, Bs):
+        assert oracle.backward_error(A, x.reshape(-1, 1), b.reshape(-1, 1)) <= 1e-6
+        Lref, _ = oracle.potrf_unblocked(A)
+        assert scaled_error(L, Lref, A) <= 1e-5
+        if A.shape[0] > 100:
+            _, f = chol.chol_mixed_factor(chol.colmajor(A), chol.opts(precision="fp32", nb=128))
+            Lm = np.tril(f.factor().cpu().numpy())
+            f.close()
+            assert np.array_equal(L, Lm), A.shape[0]
+    plan.close()
+
+
 def test_batched_tensor_core_split_order():
     """tc_min_order = 256: the matrices of order above 256 run in the
     tensor-core part and each equals the single factorization with
