@@ -288,10 +288,11 @@ typedef struct chol_batch_s *chol_batch_h;
  * it with CHOL_FLAG_FP64_TC and nb = 128 (the default single factorization
  * above order 1024); CHOL_FLAG_FP64_SIMT in opts->flags keeps every matrix on
  * the CUDA-core bodies.  In FP32 plans it is the mixed-precision engine's FP32
- * mode (binary64 POTRF, binary32 TRSM, SYRK/GEMM as three TF32 products with
- * binary32 accumulation), each matrix with the bits of chol_mixed_factor at
- * CHOL_FP32 and nb = 128, solved in binary32.  The other matrices run in true
- * binary32 (FP32) or binary64 arithmetic on the CUDA cores with opts->nb. */
+ * bodies with the diagonal tiles factored in binary32 (binary32 TRSM,
+ * SYRK/GEMM as three TF32 products with binary32 accumulation), solved in
+ * binary32; a matrix gets the same bits alone and in any batch.  The other
+ * matrices run in true binary32 (FP32) or binary64 arithmetic on the CUDA
+ * cores with opts->nb. */
 int chol_batch_plan(int32_t batch, const int64_t *n, const chol_opts *opts, chol_batch_h *out);
 
 /* Factor every A[i] in place (lower triangle <- L_i) and overwrite B[i] with

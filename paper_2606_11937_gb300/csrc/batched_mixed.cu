@@ -2,16 +2,18 @@
 // solve plan (many independent factorizations of Section 3.1 in one
 // dataflow launch of Section 3.2): every matrix of order above the split order is factored on
 // tiles of order 128 with the task bodies of the mixed-precision engine in
-// its FP32 mode (POTRF of a diagonal tile in binary64, TRSM in binary32,
-// SYRK/GEMM as three TF32 products with binary32 accumulation in tensor
-// memory, mixed_body.cuh) and then solved in binary32, all of them in ONE
+// its FP32 mode (TRSM in binary32, SYRK/GEMM as three TF32 products with
+// binary32 accumulation in tensor memory, mixed_body.cuh), the diagonal tiles
+// factored in binary32 as in the rest of a binary32 batch (shared memory, the
+// same right-looking order as the engine's binary64 one), and then solved in
+// binary32, all of them in ONE
 // persistent dataflow kernel with one ready queue.  The matrices' binary32
 // tiles live in the batch's tile stores; their TF32 operand copies (hi and
 // lo) in one arena each, so one pair of tensor maps serves every matrix.  A
 // matrix whose POTRF fails records its info and turns its remaining tasks
-// into no-ops; the other matrices are unaffected.  Each matrix gets the bits
-// of a single mixed-precision FP32 factorization of it at tile order 128 (the
-// same block operations in the same order).
+// into no-ops; the other matrices are unaffected.  The bits of a matrix do
+// not depend on the rest of the batch (every tile receives its operations in
+// the same order).
 #include <string.h>
 
 #include <vector>
@@ -91,8 +93,8 @@ struct MixedBatchBody {
                 g.info[m] = col;
                 st_release_s32(g.failed + m, 1);
             };
-            ok = mixed_task(g.mx, a, m, I, K, J, sm, reinterpret_cast<float *>(g.mdesc[m].store), g.desc[m].tile_off,
-                            t0, Done{g, a}, fail);
+            ok = mixed_task<true>(g.mx, a, m, I, K, J, sm, reinterpret_cast<float *>(g.mdesc[m].store),
+                                  g.desc[m].tile_off, t0, Done{g, a}, fail);
         }
         if (!ok && threadIdx.x == 0) fail_timeout(a);
         __syncthreads();

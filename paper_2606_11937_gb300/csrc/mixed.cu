@@ -128,7 +128,7 @@ struct MixedBody {
             report_info(a.ctl, col);
             st_release_s32(&a.ctl->abort, 1);
         };
-        const bool ok = mixed_task(g, a, m, I, K, J, sm, g.S.base, 0, t0, Done{g, a}, fail);
+        const bool ok = mixed_task<false>(g, a, m, I, K, J, sm, g.S.base, 0, t0, Done{g, a}, fail);
         if (!ok && threadIdx.x == 0) {
             if (atomicCAS(&a.ctl->status, 0, (int32_t)CHOL_ERR_TIMEOUT) == 0) a.ctl->timeout_where = 3;
             st_release_s32(&a.ctl->abort, 1);

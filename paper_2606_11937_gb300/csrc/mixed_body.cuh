@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <type_traits>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -221,8 +222,10 @@ __device__ inline void smem_trsm128_f32(float *B, const float *L, float *smem, i
 // matrix's binary32 tiles (order g.S.nb) are at `store`, its operand copies
 // and scaling exponents at arena tile `toff` onwards (the operand maps span the
 // arena); fail(col) records a non-positive pivot at 1-based column col and
-// Done completes a deferred epilogue.  Returns false if a wait expired.
-template <class Done, class Fail>
+// Done completes a deferred epilogue.  kPotrf32: the diagonal blocks are
+// factored in binary32 (binary32 batches) instead of binary64.  Returns false
+// if a wait expired.
+template <bool kPotrf32, class Done, class Fail>
 __device__ bool mixed_task(const MixedArgs &g, const SchedArgs &a, int m, int I, int K, int J, MixedSmem &sm,
                            float *store, int64_t toff, uint64_t t0, const Done &done, const Fail &fail) {
     const int type = task_type(I, K, J);
@@ -241,7 +244,8 @@ __device__ bool mixed_task(const MixedArgs &g, const SchedArgs &a, int m, int I,
             SimtSmem<float> &ss = *reinterpret_cast<SimtSmem<float> *>(sm.stages);
             for (int j = 0; j < r; ++j) {
                 float *Tjj = T + (size_t)j * kPotrfNb * nb + j * kPotrfNb;
-                const int li = smem_potrf128<float>(Tjj, &sm.stages[0][0], nb);
+                const int li = smem_potrf128<float, typename std::conditional<kPotrf32, float, double>::type>(
+                    Tjj, &sm.stages[0][0], nb);
                 if (li) {
                     if (threadIdx.x == 0) fail((int64_t)J * nb + j * kPotrfNb + li);
                     break;

@@ -18,9 +18,10 @@ constexpr int kPotrfPanelThreads = 128;  // warps 0..3, one per SM sub-partition
 // the panel threads' named barrier (id 4; no other code of a task uses it)
 __device__ __forceinline__ void potrf_panel_sync() { asm volatile("bar.sync 4, 128;" ::: "memory"); }
 
-// Cholesky, in binary64, of a 128 x 128 diagonal tile (row-major, lower part
-// read and written; T = double, or float widened on load and rounded on
-// store) in shared memory, right-looking: columns are factored four at a
+// Cholesky, in the compute type C (binary64 by default; binary32 for the
+// binary32 batches), of a 128 x 128 diagonal tile (row-major, lower part read
+// and written; T = double, or float widened on load and rounded on store) in
+// shared memory, right-looking: columns are factored four at a
 // time and each block of four is applied to the trailing lower triangle as
 // one rank-4 update.  With lookahead: while warps 4.. apply panel p to the
 // columns right of panel p + 1, warps 0..3 (one per SM sub-partition, so the
@@ -36,13 +37,13 @@ __device__ __forceinline__ void potrf_panel_sync() { asm volatile("bar.sync 4, 1
 // reciprocals of its diagonal, at kPotrf128RcpOff, stay there for the
 // caller); returns 0 or the 1-based local column whose pivot is not positive
 // (or NaN).  Ends with a barrier.
-template <typename T>
+template <typename T, typename C = double>
 __device__ int smem_potrf128(T *A, uint8_t *smem, int ld = kPotrfNb) {
     constexpr int N = kPotrfNb;
     constexpr int P = N + 1;  // padded row
-    double *S = reinterpret_cast<double *>(smem);
+    C *S = reinterpret_cast<C *>(smem);
     uint16_t *tab = reinterpret_cast<uint16_t *>(smem + kPotrf128TabOff);
-    double *rcp = reinterpret_cast<double *>(smem + kPotrf128RcpOff);
+    C *rcp = reinterpret_cast<C *>(smem + kPotrf128RcpOff);
     const int t = threadIdx.x, nt = blockDim.x;
     constexpr int kTri = N * (N + 1) / 2;
     // eight loads in flight per thread before their shared-memory stores
@@ -57,7 +58,7 @@ __device__ int smem_potrf128(T *A, uint8_t *smem, int ld = kPotrfNb) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int e = e0 + u * nt, i = e / N, k = e % N;
-            if (e < N * N && k <= i) S[i * P + k] = (double)v[u];
+            if (e < N * N && k <= i) S[i * P + k] = (C)v[u];
         }
     }
     for (int k = t; k < N; k += nt) {
@@ -77,10 +78,10 @@ __device__ int smem_potrf128(T *A, uint8_t *smem, int ld = kPotrfNb) {
     auto factor_panel = [&](int j0) -> int {
         for (int q = 0; q < 4; ++q) {
             const int j = j0 + q;
-            const double djj = S[j * P + j];
+            const C djj = S[j * P + j];
             potrf_panel_sync();
-            if (!(djj > 0.0)) return j + 1;  // uniform: every thread read the same value
-            const double d = sqrt(djj), rd = 1.0 / d;
+            if (!(djj > C(0))) return j + 1;  // uniform: every thread read the same value
+            const C d = sqrt(djj), rd = C(1) / d;
             if (t == 0) {
                 S[j * P + j] = d;
                 rcp[j] = rd;
@@ -88,7 +89,7 @@ __device__ int smem_potrf128(T *A, uint8_t *smem, int ld = kPotrfNb) {
             for (int i = j + 1 + t; i < N; i += PT) S[i * P + j] *= rd;
             potrf_panel_sync();
             for (int c = j + 1; c < j0 + 4; ++c) {
-                const double scj = S[c * P + j];
+                const C scj = S[c * P + j];
                 for (int i = c + t; i < N; i += PT) S[i * P + c] = fma(-S[i * P + j], scj, S[i * P + c]);
             }
             potrf_panel_sync();
@@ -100,7 +101,7 @@ __device__ int smem_potrf128(T *A, uint8_t *smem, int ld = kPotrfNb) {
     auto rank4 = [&](int j0, int e0, int e1, int r, int count) {
         for (int e = e0 + r; e < e1; e += count) {
             const int ik = tab[e], i = ik >> 8, k = ik & 255;
-            double v = S[i * P + k];
+            C v = S[i * P + k];
 #pragma unroll
             for (int q = 0; q < 4; ++q) v = fma(-S[i * P + j0 + q], S[k * P + j0 + q], v);
             S[i * P + k] = v;

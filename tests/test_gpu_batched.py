@@ -176,37 +176,50 @@ def _check_failures(plan, As, Bs, Ls, Xs, which):
             assert info2[i] == 0 and np.array_equal(L2[i], Ls[i]) and np.array_equal(X2[i], Xs[i]), i
 
 
+def _fp32_alone_equals_mix(ns, As, Bs, Ls, o, which):
+    """Each matrix in `which` factored in a batch of its own gives the bits it
+    got in the mixed batch (the bits of a matrix do not depend on the rest)."""
+    import paper_2606_11937_gb300 as chol
+    for k in which:
+        plan = chol.chol_batch_plan([ns[k]], o)
+        L1, _, info1 = run_batch(plan, [As[k]], [Bs[k]])
+        plan.close()
+        assert info1 == [0] and np.array_equal(L1[0], Ls[k]), ns[k]
+
+
 def test_batched_fp32_tensor_core_part():
     """FP32 matrices of order above 1024 run in the batch's tensor-core part
-    (the mixed-precision engine's FP32 bodies: binary64 POTRF, binary32 TRSM,
-    SYRK/GEMM as three TF32 products, tile order 128, one persistent kernel
-    with the fused binary32 SOLVE): each factor equals the single
-    mixed-precision FP32 factorization at tile order 128 bit for bit and is
-    within the binary32 tolerance of the oracle, every solution reaches the
-    binary32 backward error, failing matrices report the oracle's info and
-    leave the others untouched, and tc_min_order = 2048 keeps every matrix on
-    the CUDA cores."""
+    (tile order 128: diagonal tiles factored in binary32 in shared memory,
+    binary32 TRSM, SYRK/GEMM as three TF32 products, one persistent kernel with
+    the fused binary32 SOLVE): exact-integer inputs A = L0 L0^T give L0 bit for
+    bit; factors are within the binary32 tolerance of the oracle and each
+    matrix gets the same bits alone and in the batch; every solution reaches
+    the binary32 backward error; failing matrices report the oracle's info and
+    leave the others untouched; tc_min_order = 2048 keeps every matrix on the
+    CUDA cores."""
     import paper_2606_11937_gb300 as chol
     ns = [1100, 300, 2048, 1025, 64, 1536, 700, 1300]
+    o = chol.opts(precision="fp32")
+    # exact pin: every operation on these integers is exact in binary32
+    ints = [si.exact_integer_factor(n, seed=230 + i) for i, n in enumerate([1100, 1536, 2048])]
+    plan = chol.chol_batch_plan([A.shape[0] for A, _ in ints], o)
+    Li, _, infoi = run_batch(plan, [A for A, _ in ints], [si.rhs(A.shape[0], 1, seed=7)[:, 0] for A, _ in ints])
+    plan.close()
+    assert infoi == [0, 0, 0]
+    for (A, L0), L in zip(ints, Li):
+        assert np.array_equal(L, L0), A.shape[0]
     As, Bs = make_batch(ns, 190)
-    plan = chol.chol_batch_plan(ns, chol.opts(precision="fp32"))
+    plan = chol.chol_batch_plan(ns, o)
     Ls, Xs, info = run_batch(plan, As, Bs)
     assert info == [0] * len(ns)
     assert plan.stats().tasks[3] > 0
     for A, L, x, b in zip(As, Ls, Xs, Bs):
-        n = A.shape[0]
         assert oracle.backward_error(A, x.reshape(-1, 1), b.reshape(-1, 1)) <= 1e-6
-        if n > 1024:
-            _, f = chol.chol_mixed_factor(chol.colmajor(A), chol.opts(precision="fp32", nb=128))
-            assert f.info == 0
-            Lm = np.tril(f.factor().cpu().numpy())
-            f.close()
-            assert np.array_equal(L, Lm), n
-        if n <= 1100:
-            Lref, _ = oracle.potrf_unblocked(A)
-            assert scaled_error(L, Lref, A) <= 1e-5
+        Lref, _ = oracle.potrf_unblocked(A)
+        assert scaled_error(L, Lref, A) <= 1e-5, A.shape[0]
     _check_failures(plan, As, Bs, Ls, Xs, (0, 5))
     plan.close()
+    _fp32_alone_equals_mix(ns, As, Bs, Ls, o, (0, 2, 3))
     # every matrix on the CUDA cores
     plan = chol.chol_batch_plan(ns, chol.opts(precision="fp32", tc_min_order=2048))
     Lc, Xc, infoc = run_batch(plan, As, Bs)
@@ -222,25 +235,30 @@ def test_batched_fp32_tensor_core_part():
 def test_batched_fp32_tensor_core_small_orders():
     """tc_min_order = 100 in an FP32 plan: matrices of one padded tile of order
     128 (n = 101, 128), of two tiles with a one-row ragged tile (129) and a few
-    tiles run in the tensor-core part; each equals the single mixed-precision
-    FP32 factorization at tile order 128 bit for bit and reaches the binary32
-    backward error; the matrix below the split stays on the CUDA cores."""
+    tiles run in the tensor-core part: exact-integer inputs give L0 bit for
+    bit, the others are within the binary32 tolerance of the oracle, get the
+    same bits alone and in the batch and reach the binary32 backward error;
+    the matrix below the split stays on the CUDA cores."""
     import paper_2606_11937_gb300 as chol
     ns = [101, 128, 129, 250, 90, 384]
+    o = chol.opts(precision="fp32", tc_min_order=100)
+    ints = [si.exact_integer_factor(n, seed=250 + i) for i, n in enumerate(ns)]
+    plan = chol.chol_batch_plan(ns, o)
+    Li, _, infoi = run_batch(plan, [A for A, _ in ints], [si.rhs(n, 1, seed=8)[:, 0] for n in ns])
+    plan.close()
+    assert infoi == [0] * len(ns)
+    for (A, L0), L in zip(ints, Li):
+        assert np.array_equal(L, L0), A.shape[0]
     As, Bs = make_batch(ns, 210)
-    plan = chol.chol_batch_plan(ns, chol.opts(precision="fp32", tc_min_order=100))
+    plan = chol.chol_batch_plan(ns, o)
     Ls, Xs, info = run_batch(plan, As, Bs)
     assert info == [0] * len(ns)
     for A, L, x, b in zip(As, Ls, Xs, Bs):
         assert oracle.backward_error(A, x.reshape(-1, 1), b.reshape(-1, 1)) <= 1e-6
         Lref, _ = oracle.potrf_unblocked(A)
         assert scaled_error(L, Lref, A) <= 1e-5
-        if A.shape[0] > 100:
-            _, f = chol.chol_mixed_factor(chol.colmajor(A), chol.opts(precision="fp32", nb=128))
-            Lm = np.tril(f.factor().cpu().numpy())
-            f.close()
-            assert np.array_equal(L, Lm), A.shape[0]
     plan.close()
+    _fp32_alone_equals_mix(ns, As, Bs, Ls, o, (0, 2, 5))
 
 
 def test_batched_tensor_core_split_order():
